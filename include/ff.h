@@ -1,0 +1,215 @@
+/*
+ * ff.h -- C ABI of the GB300 float-float library (libff.so).
+ *
+ * Float-float arithmetic after Da Graca & Defour, "Implementation of
+ * float-float operators on graphics hardware" (arXiv cs/0603115): a number is
+ * the unevaluated sum hi + lo of two IEEE binary32 values (Section 4,
+ * "Proposed format"), about 44 bits of precision with the exponent range of
+ * binary32 (Section 7).
+ *
+ * Conventions that hold for every entry point unless its comment says
+ * otherwise:
+ *   - Memory.  Every array argument is a DEVICE pointer owned by the caller,
+ *     at least 8-byte aligned (the alignment of ff2); 16-byte alignment is
+ *     not required.  The library never allocates device memory inside a
+ *     call: scratch space is a caller-owned workspace whose size the matching
+ *     *_workspace_bytes() function returns.
+ *   - Streams.  Calls only enqueue work on the caller's stream `s` (0 = the
+ *     legacy default stream) and return at once; results, including the
+ *     scalar result of a reduction, stay on the device.  No call
+ *     synchronises.  A call is safe to capture in a CUDA graph when its
+ *     arguments stay valid for the graph's lifetime.
+ *   - Errors.  Arguments are checked on the host before anything is
+ *     enqueued: a NULL pointer with n > 0, a pointer not 8-byte aligned, a
+ *     negative size or stride, or a stride smaller than its extent returns
+ *     FF_ERR_INVALID_ARG; a workspace that is NULL or too small returns
+ *     FF_ERR_WORKSPACE.  A failed launch returns FF_ERR_CUDA and keeps the
+ *     CUDA error code for ff_last_cuda_error().  Nothing is enqueued when a
+ *     call returns an error.
+ *   - Sizes.  n == 0 is a no-op returning FF_OK, except that a reduction
+ *     with n == 0 writes (0, 0) to its result.
+ *   - Aliasing.  An elementwise output may be exactly one of its inputs
+ *     (in place); any other overlap is undefined.
+ *   - Results.  Every elementwise result is the exact op sequence of the
+ *     cited algorithm in binary32 round-to-nearest-even, with subnormals
+ *     kept: bit-for-bit reproducible.  Reductions follow the fixed tree order
+ *     documented with ff_sum and are bit-for-bit reproducible for a given n,
+ *     device and build.
+ */
+#ifndef FF_GB300_H
+#define FF_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#if defined(__GNUC__)
+#define FF_API __attribute__((visibility("default")))
+#else
+#define FF_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* One float-float value, layout-compatible with CUDA float2: hi in x, lo in
+ * y.  For the error-free transformations an ff2 is also used for a packed
+ * pair of binary32 operands (a, b) or results (s, e). */
+typedef struct ff2 {
+    float hi;
+    float lo;
+} ff2;
+
+typedef enum ff_status {
+    FF_OK = 0,
+    FF_ERR_INVALID_ARG = 1,
+    FF_ERR_WORKSPACE = 2,
+    FF_ERR_CUDA = 3,
+    FF_ERR_TIMEOUT = 4,
+    FF_ERR_UNSUPPORTED = 5
+} ff_status;
+
+/* ------------------------------------------------------------------------ */
+/* Error-free transformations (Section 4.1)                                  */
+/* ------------------------------------------------------------------------ */
+
+/* Add12 theorem (Knuth, branch free): for each i, with (a, b) = ab[i],
+ * se[i] = (s, e) where s = RN(a + b) and s + e = a + b exactly.
+ * ab: n packed binary32 operand pairs; se: n result pairs. */
+FF_API ff_status ff_add12(const ff2* ab, ff2* se, size_t n, cudaStream_t s);
+
+/* Mul12 theorem (Dekker): for each i, pe[i] = (p, e) with p = RN(a * b) and
+ * p + e = a * b exactly (no under- or overflow).  Computed as
+ * e = fma(a, b, -p), equal to the paper's Split form wherever both are
+ * defined. */
+FF_API ff_status ff_mul12(const ff2* ab, ff2* pe, size_t n, cudaStream_t s);
+
+/* ------------------------------------------------------------------------ */
+/* Float-float operators (elementwise, n values each)                        */
+/* ------------------------------------------------------------------------ */
+
+/* Add22 theorem: out[i] = Add22(a[i], b[i]),
+ * |err| <= max(2^-24 |al + bl|, 2^-44 |a + b|). */
+FF_API ff_status ff_add(const ff2* a, const ff2* b, ff2* out, size_t n, cudaStream_t s);
+
+/* Mul22 theorem: out[i] = Mul22(a[i], b[i]), relative error <= 2^-44. */
+FF_API ff_status ff_mul(const ff2* a, const ff2* b, ff2* out, size_t n, cudaStream_t s);
+
+/* Division a[i] / b[i] (not in the paper; Dekker's div2, the construction the
+ * paper's Split and Mul12 come from, finished with the paper's Add12).
+ * Divisors are expected to satisfy |b.hi| >= 2^-60; b.hi == 0 gives the IEEE
+ * infinities or NaN of ah / bh. */
+FF_API ff_status ff_div(const ff2* a, const ff2* b, ff2* out, size_t n, cudaStream_t s);
+
+/* Square root of a[i] (not in the paper; Dekker's sqrt2 finished with
+ * Add12).  a.hi == +-0 gives (a.hi, 0); a.hi < 0 gives (NaN, NaN). */
+FF_API ff_status ff_sqrt(const ff2* a, ff2* out, size_t n, cudaStream_t s);
+
+/* z[i] = Add22(Mul22(alpha, x[i]), y[i]); alpha is passed by value. */
+FF_API ff_status ff_axpy(ff2 alpha, const ff2* x, const ff2* y, ff2* z, size_t n, cudaStream_t s);
+
+/* ------------------------------------------------------------------------ */
+/* Compensated reductions (Section 7's "compensated algorithms")             */
+/* ------------------------------------------------------------------------ */
+
+/* Workspace bytes for ff_sum / ff_dot / ff_f64_dot on the current device
+ * (independent of n above a small size; always > 0). */
+FF_API size_t ff_reduce_workspace_bytes(size_t n);
+
+/* *out_dev = the float-float sum of x[0..n) by Add22.  Order: thread t of a
+ * grid of T threads accumulates, left to right, its elements of a
+ * grid-stride sweep over the array (in two-value chunks), starting from
+ * (0, 0); each warp then combines its 32 lanes by a shuffle-down tree, each
+ * block its warps likewise, and the last block to finish combines the
+ * per-block partials in block order.  ws: caller-owned device workspace of
+ * at least ff_reduce_workspace_bytes(n) bytes, 16-byte aligned; it is
+ * written by the call and must not be used concurrently by another call.
+ * Error bound for the stored result r: |r - sum x_i| <= n 2^-46 sum |x_i|. */
+FF_API ff_status ff_sum(const ff2* x, size_t n, ff2* out_dev, void* ws, size_t ws_bytes, cudaStream_t s);
+
+/* *out_dev = sum_i Mul22(x[i], y[i]) with the same Add22 tree as ff_sum.
+ * |r - sum x_i y_i| <= n 2^-46 sum |x_i y_i|. */
+FF_API ff_status ff_dot(const ff2* x, const ff2* y, size_t n, ff2* out_dev, void* ws, size_t ws_bytes,
+                 cudaStream_t s);
+
+/* Launch shape ff_sum / ff_dot use for these arguments (nothing is
+ * launched): *grid blocks of 256 threads; *head = 1 when one leading element
+ * is accumulated alone by thread 0 to reach a 16-byte boundary; *vector = 1
+ * for the two-value chunk sweep, 0 for the one-value sweep used when x and y
+ * have different offsets modulo 16 bytes.  y may be NULL (ff_sum).  Lets a
+ * caller reproduce the documented combination order exactly. */
+FF_API ff_status ff_reduce_launch_shape(const ff2* x, const ff2* y, size_t n, unsigned* grid, int* head,
+                                        int* vector);
+
+/* Adjoint of d = ff_dot(x, y): given the float-float cotangent *dout_dev
+ * (device), dx[i] = Mul22(dout, y[i]) and dy[i] = Mul22(dout, x[i]).  The
+ * gradient of a float-float value is a float-float value holding
+ * dL/d(hi + lo). */
+FF_API ff_status ff_dot_backward(const ff2* dout_dev, const ff2* x, const ff2* y, ff2* dx, ff2* dy,
+                          size_t n, cudaStream_t s);
+
+/* ------------------------------------------------------------------------ */
+/* Float-float GEMV and its adjoint                                          */
+/* ------------------------------------------------------------------------ */
+
+/* Y = A X, Mul22 per term, Add22 accumulation.  A: m x n row-major with row
+ * stride lda >= n (elements); X: n x k column-major, column stride ldx >= n;
+ * Y: m x k column-major, column stride ldy >= m.  1 <= k <= 64. */
+FF_API ff_status ff_gemv(const ff2* A, int64_t m, int64_t n, int64_t lda, const ff2* X, int64_t ldx,
+                  int64_t k, ff2* Y, int64_t ldy, cudaStream_t s);
+
+/* Workspace bytes for ff_gemv_t on the current device. */
+FF_API size_t ff_gemv_t_workspace_bytes(int64_t m, int64_t n, int64_t k);
+
+/* dX = A^T dY (the adjoint of ff_gemv with respect to X).  dY: m x k
+ * column-major (stride lddy >= m); dX: n x k column-major (stride
+ * lddx >= n).  Row blocks of A are reduced separately into the workspace,
+ * then combined in row-block order.  1 <= k <= 64. */
+FF_API ff_status ff_gemv_t(const ff2* A, int64_t m, int64_t n, int64_t lda, const ff2* dY,
+                    int64_t lddy, int64_t k, ff2* dX, int64_t lddx, void* ws, size_t ws_bytes,
+                    cudaStream_t s);
+
+/* ------------------------------------------------------------------------ */
+/* Native baselines on the same GPU (measurement only)                       */
+/* ------------------------------------------------------------------------ */
+
+/* Binary64: out[i] = a[i] op b[i] (op = +, *, /) and sqrt(a[i]). */
+FF_API ff_status ff_f64_add(const double* a, const double* b, double* out, size_t n, cudaStream_t s);
+FF_API ff_status ff_f64_mul(const double* a, const double* b, double* out, size_t n, cudaStream_t s);
+FF_API ff_status ff_f64_div(const double* a, const double* b, double* out, size_t n, cudaStream_t s);
+FF_API ff_status ff_f64_sqrt(const double* a, double* out, size_t n, cudaStream_t s);
+/* Binary64 dot product (fma accumulation, same tree shape as ff_dot). */
+FF_API ff_status ff_f64_dot(const double* x, const double* y, size_t n, double* out_dev, void* ws,
+                     size_t ws_bytes, cudaStream_t s);
+/* Binary64 GEMV, same layouts as ff_gemv. */
+FF_API ff_status ff_f64_gemv(const double* A, int64_t m, int64_t n, int64_t lda, const double* X,
+                      int64_t ldx, int64_t k, double* Y, int64_t ldy, cudaStream_t s);
+
+/* Plain binary32 add, multiply and multiply-add (two roundings), the
+ * normalisation baseline of the paper's timing tables (Section 6). */
+FF_API ff_status ff_f32_add(const float* a, const float* b, float* out, size_t n, cudaStream_t s);
+FF_API ff_status ff_f32_mul(const float* a, const float* b, float* out, size_t n, cudaStream_t s);
+FF_API ff_status ff_f32_mad(const float* a, const float* b, const float* c, float* out, size_t n,
+                     cudaStream_t s);
+
+/* ------------------------------------------------------------------------ */
+/* Status                                                                    */
+/* ------------------------------------------------------------------------ */
+
+/* Static string naming a status code. */
+FF_API const char* ff_status_string(ff_status st);
+
+/* The CUDA error code kept by the last call of this thread that returned
+ * FF_ERR_CUDA (0 if none); returns FF_OK, or FF_ERR_INVALID_ARG for a NULL
+ * argument. */
+FF_API ff_status ff_last_cuda_error(int* cuda_err);
+
+/* A string identifying this build (used to key autotuning caches). */
+FF_API const char* ff_build_id(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FF_GB300_H */

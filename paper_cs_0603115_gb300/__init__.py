@@ -1,0 +1,346 @@
+"""GB300 float-float arithmetic (Da Graca & Defour, arXiv cs/0603115).
+
+A float-float tensor is a ``torch.float32`` CUDA tensor whose last dimension
+is 2: ``x[..., 0]`` is the high part and ``x[..., 1]`` the low part of the
+unevaluated sum hi + lo (Section 4 of the paper).  Vectors are ``(n, 2)``.
+Every function here marshals its arguments and calls one entry point of the
+C ABI in ``libff.so`` (include/ff.h) on the current CUDA stream; all
+arithmetic runs in the library's CUDA kernels.  Nothing falls back to the CPU:
+a missing library or a non-CUDA tensor raises.
+
+Elementwise:  add12, mul12 (packed (a, b) pairs), add, mul, div, sqrt, axpy
+Reductions:   sum, dot (device-resident float-float result), dot_backward
+GEMV:         gemv (Y = A X), gemv_t (dX = A^T dY)
+Autograd:     FFDot, FFGemv (hand-written adjoint kernels)
+Baselines:    f64_add/mul/div/sqrt/dot/gemv, f32_add/mul/mad
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib
+from ._lib import FFError, ff2
+
+__all__ = [
+    "add12", "mul12", "add", "mul", "div", "sqrt", "axpy", "sum", "dot", "dot_backward",
+    "gemv", "gemv_t", "FFDot", "FFGemv", "ffdot", "ffgemv", "FFError", "workspace",
+    "f64_add", "f64_mul", "f64_div", "f64_sqrt", "f64_dot", "f64_gemv", "f32_add", "f32_mul",
+    "f32_mad", "load",
+]
+
+
+def load():
+    """Load libff.so (raises if it is not built)."""
+    return _lib.load()
+
+
+def _stream() -> int:
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _ptr(t: torch.Tensor) -> int:
+    return t.data_ptr()
+
+
+def _check_ff(t: torch.Tensor, name: str) -> None:
+    if not t.is_cuda:
+        raise ValueError(f"{name}: expected a CUDA tensor")
+    if t.dtype != torch.float32 or t.dim() < 1 or t.shape[-1] != 2:
+        raise ValueError(f"{name}: expected float32 with a last dimension of 2, got {t.dtype} {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: expected a contiguous tensor")
+
+
+def _nvals(t: torch.Tensor) -> int:
+    return t.numel() // 2
+
+
+# ---------------------------------------------------------------------------
+# workspace (caller-owned device scratch, cached per device)
+# ---------------------------------------------------------------------------
+_ws_cache: dict = {}
+
+
+def workspace(nbytes: int, device=None, key: str = "reduce") -> torch.Tensor:
+    """A cached uint8 device buffer of at least ``nbytes`` (16-byte aligned).
+
+    Buffers are shared by calls on the same device and key: do not run two
+    reductions that share one concurrently on different streams."""
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    k = (dev.index, key)
+    buf = _ws_cache.get(k)
+    if buf is None or buf.numel() < nbytes:
+        buf = torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=dev)
+        _ws_cache[k] = buf
+    return buf
+
+
+# ---------------------------------------------------------------------------
+# elementwise
+# ---------------------------------------------------------------------------
+def _unary(name, x, out):
+    _check_ff(x, name)
+    if out is None:
+        out = torch.empty_like(x)
+    _check_ff(out, name)
+    if out.shape != x.shape:
+        raise ValueError(f"{name}: output shape mismatch")
+    _lib.call(name, _ptr(x), _ptr(out), _nvals(x), _stream())
+    return out
+
+
+def _binary(name, a, b, out):
+    _check_ff(a, name)
+    _check_ff(b, name)
+    if a.shape != b.shape:
+        raise ValueError(f"{name}: shape mismatch {tuple(a.shape)} vs {tuple(b.shape)}")
+    if out is None:
+        out = torch.empty_like(a)
+    _check_ff(out, name)
+    if out.shape != a.shape:
+        raise ValueError(f"{name}: output shape mismatch")
+    _lib.call(name, _ptr(a), _ptr(b), _ptr(out), _nvals(a), _stream())
+    return out
+
+
+def add12(ab, out=None):
+    """Add12 on packed binary32 pairs: (s, e), s = RN(a + b), s + e = a + b."""
+    return _unary("ff_add12", ab, out)
+
+
+def mul12(ab, out=None):
+    """Mul12 on packed binary32 pairs: (p, e), p = RN(a b), p + e = a b."""
+    return _unary("ff_mul12", ab, out)
+
+
+def add(a, b, out=None):
+    """Add22: float-float a + b."""
+    return _binary("ff_add", a, b, out)
+
+
+def mul(a, b, out=None):
+    """Mul22: float-float a * b."""
+    return _binary("ff_mul", a, b, out)
+
+
+def div(a, b, out=None):
+    """Div22: float-float a / b."""
+    return _binary("ff_div", a, b, out)
+
+
+def sqrt(a, out=None):
+    """Sqrt22: float-float sqrt(a)."""
+    return _unary("ff_sqrt", a, out)
+
+
+def axpy(alpha, x, y, out=None):
+    """z = Add22(Mul22(alpha, x), y); alpha is a (hi, lo) pair of floats."""
+    _check_ff(x, "ff_axpy")
+    _check_ff(y, "ff_axpy")
+    if x.shape != y.shape:
+        raise ValueError("ff_axpy: shape mismatch")
+    if out is None:
+        out = torch.empty_like(x)
+    hi, lo = (float(alpha[0]), float(alpha[1]))
+    _lib.call("ff_axpy", ff2(hi, lo), _ptr(x), _ptr(y), _ptr(out), _nvals(x), _stream())
+    return out
+
+
+# ---------------------------------------------------------------------------
+# reductions
+# ---------------------------------------------------------------------------
+def _reduce_ws(n: int, device) -> torch.Tensor:
+    return workspace(_lib.load().ff_reduce_workspace_bytes(n), device)
+
+
+def sum(x, out=None):  # noqa: A001  (mirrors the C name ff_sum)
+    """Float-float sum of an (n, 2) vector; returns a (2,) device tensor."""
+    _check_ff(x, "ff_sum")
+    if out is None:
+        out = torch.empty(2, dtype=torch.float32, device=x.device)
+    n = _nvals(x)
+    ws = _reduce_ws(n, x.device)
+    _lib.call("ff_sum", _ptr(x), n, _ptr(out), _ptr(ws), ws.numel(), _stream())
+    return out
+
+
+def dot(x, y, out=None):
+    """Float-float dot product sum_i Mul22(x_i, y_i); returns (2,) on device."""
+    _check_ff(x, "ff_dot")
+    _check_ff(y, "ff_dot")
+    if x.shape != y.shape:
+        raise ValueError("ff_dot: shape mismatch")
+    if out is None:
+        out = torch.empty(2, dtype=torch.float32, device=x.device)
+    n = _nvals(x)
+    ws = _reduce_ws(n, x.device)
+    _lib.call("ff_dot", _ptr(x), _ptr(y), n, _ptr(out), _ptr(ws), ws.numel(), _stream())
+    return out
+
+
+def dot_backward(dout, x, y, dx=None, dy=None):
+    """dx = Mul22(dout, y), dy = Mul22(dout, x); dout is a (2,) device tensor."""
+    _check_ff(dout, "ff_dot_backward")
+    _check_ff(x, "ff_dot_backward")
+    _check_ff(y, "ff_dot_backward")
+    if dx is None:
+        dx = torch.empty_like(x)
+    if dy is None:
+        dy = torch.empty_like(y)
+    _lib.call("ff_dot_backward", _ptr(dout), _ptr(x), _ptr(y), _ptr(dx), _ptr(dy), _nvals(x), _stream())
+    return dx, dy
+
+
+# ---------------------------------------------------------------------------
+# GEMV
+# ---------------------------------------------------------------------------
+def gemv(A, X, out=None):
+    """Y = A X.  A: (m, n, 2) row-major; X: (k, n, 2), i.e. n x k column-major
+    (X[c] is right-hand side c).  Returns Y as (k, m, 2)."""
+    _check_ff(A, "ff_gemv")
+    _check_ff(X, "ff_gemv")
+    if A.dim() != 3 or X.dim() != 3 or X.shape[1] != A.shape[1]:
+        raise ValueError("ff_gemv: expected A (m, n, 2) and X (k, n, 2)")
+    m, n = A.shape[0], A.shape[1]
+    k = X.shape[0]
+    if out is None:
+        out = torch.empty((k, m, 2), dtype=torch.float32, device=A.device)
+    _lib.call("ff_gemv", _ptr(A), m, n, n, _ptr(X), n, k, _ptr(out), m, _stream())
+    return out
+
+
+def gemv_t(A, dY, out=None):
+    """dX = A^T dY.  A: (m, n, 2); dY: (k, m, 2).  Returns dX as (k, n, 2)."""
+    _check_ff(A, "ff_gemv_t")
+    _check_ff(dY, "ff_gemv_t")
+    if A.dim() != 3 or dY.dim() != 3 or dY.shape[1] != A.shape[0]:
+        raise ValueError("ff_gemv_t: expected A (m, n, 2) and dY (k, m, 2)")
+    m, n = A.shape[0], A.shape[1]
+    k = dY.shape[0]
+    if out is None:
+        out = torch.empty((k, n, 2), dtype=torch.float32, device=A.device)
+    nbytes = _lib.load().ff_gemv_t_workspace_bytes(m, n, k)
+    ws = workspace(nbytes, A.device, key="gemv_t")
+    _lib.call("ff_gemv_t", _ptr(A), m, n, n, _ptr(dY), m, k, _ptr(out), n, _ptr(ws), ws.numel(), _stream())
+    return out
+
+
+# ---------------------------------------------------------------------------
+# autograd: hand-written adjoints
+# ---------------------------------------------------------------------------
+class FFDot(torch.autograd.Function):
+    """d = dot(x, y) with the adjoint kernel ff_dot_backward.  The gradient of
+    a float-float tensor is a float-float tensor holding dL/d(hi + lo).  The
+    backward reuses the inputs themselves (saved by reference); nothing else
+    is stored."""
+
+    @staticmethod
+    def forward(ctx, x, y):
+        ctx.save_for_backward(x, y)
+        return dot(x, y)
+
+    @staticmethod
+    def backward(ctx, dout):
+        x, y = ctx.saved_tensors
+        dout = dout.contiguous()
+        dx, dy = dot_backward(dout, x, y)
+        return (dx if ctx.needs_input_grad[0] else None, dy if ctx.needs_input_grad[1] else None)
+
+
+class FFGemv(torch.autograd.Function):
+    """Y = A X with the adjoint dX = A^T dY (A is treated as a constant)."""
+
+    @staticmethod
+    def forward(ctx, A, X):
+        ctx.save_for_backward(A)
+        return gemv(A, X)
+
+    @staticmethod
+    def backward(ctx, dY):
+        (A,) = ctx.saved_tensors
+        return None, gemv_t(A, dY.contiguous())
+
+
+def ffdot(x, y):
+    return FFDot.apply(x, y)
+
+
+def ffgemv(A, X):
+    return FFGemv.apply(A, X)
+
+
+# ---------------------------------------------------------------------------
+# native baselines
+# ---------------------------------------------------------------------------
+def _f64_check(t, name):
+    if not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise ValueError(f"{name}: expected a contiguous float64 CUDA tensor")
+
+
+def _f64_binary(name, a, b, out):
+    _f64_check(a, name)
+    _f64_check(b, name)
+    out = torch.empty_like(a) if out is None else out
+    _lib.call(name, _ptr(a), _ptr(b), _ptr(out), a.numel(), _stream())
+    return out
+
+
+def f64_add(a, b, out=None): return _f64_binary("ff_f64_add", a, b, out)
+def f64_mul(a, b, out=None): return _f64_binary("ff_f64_mul", a, b, out)
+def f64_div(a, b, out=None): return _f64_binary("ff_f64_div", a, b, out)
+
+
+def f64_sqrt(a, out=None):
+    _f64_check(a, "ff_f64_sqrt")
+    out = torch.empty_like(a) if out is None else out
+    _lib.call("ff_f64_sqrt", _ptr(a), _ptr(out), a.numel(), _stream())
+    return out
+
+
+def f64_dot(x, y, out=None):
+    _f64_check(x, "ff_f64_dot")
+    _f64_check(y, "ff_f64_dot")
+    out = torch.empty(1, dtype=torch.float64, device=x.device) if out is None else out
+    ws = _reduce_ws(x.numel(), x.device)
+    _lib.call("ff_f64_dot", _ptr(x), _ptr(y), x.numel(), _ptr(out), _ptr(ws), ws.numel(), _stream())
+    return out
+
+
+def f64_gemv(A, X, out=None):
+    """Binary64 Y = A X; A (m, n), X (k, n); returns (k, m)."""
+    _f64_check(A, "ff_f64_gemv")
+    _f64_check(X, "ff_f64_gemv")
+    m, n = A.shape
+    k = X.shape[0]
+    out = torch.empty((k, m), dtype=torch.float64, device=A.device) if out is None else out
+    _lib.call("ff_f64_gemv", _ptr(A), m, n, n, _ptr(X), n, k, _ptr(out), m, _stream())
+    return out
+
+
+def _f32_check(t, name):
+    if not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+        raise ValueError(f"{name}: expected a contiguous float32 CUDA tensor")
+
+
+def f32_add(a, b, out=None):
+    _f32_check(a, "ff_f32_add"); _f32_check(b, "ff_f32_add")
+    out = torch.empty_like(a) if out is None else out
+    _lib.call("ff_f32_add", _ptr(a), _ptr(b), _ptr(out), a.numel(), _stream())
+    return out
+
+
+def f32_mul(a, b, out=None):
+    _f32_check(a, "ff_f32_mul"); _f32_check(b, "ff_f32_mul")
+    out = torch.empty_like(a) if out is None else out
+    _lib.call("ff_f32_mul", _ptr(a), _ptr(b), _ptr(out), a.numel(), _stream())
+    return out
+
+
+def f32_mad(a, b, c, out=None):
+    for t in (a, b, c):
+        _f32_check(t, "ff_f32_mad")
+    out = torch.empty_like(a) if out is None else out
+    _lib.call("ff_f32_mad", _ptr(a), _ptr(b), _ptr(c), _ptr(out), a.numel(), _stream())
+    return out

@@ -1,0 +1,372 @@
+// ff_gemv.cu -- float-float GEMV Y = A X and its adjoint dX = A^T dY, each
+// term a Mul22 and each accumulation an Add22 (the paper's operators), plus a
+// binary64 GEMV baseline with the same layouts.
+//
+// Layouts: A is m x n row-major (row stride lda); X, dX are n x k and Y, dY
+// are m x k, all column-major (column strides ldx, lddx, ldy, lddy).
+//
+// ff_gemv: one warp per row, 8 rows per 256-thread block.  Lane l walks the
+// row in two-column steps (j = 2l + 64t, 16-byte loads of A and of each
+// column of X) and keeps KT float-float accumulators, one per right-hand
+// side of the current column tile; k > KT is processed as successive tiles.
+// The 32 lane accumulators are combined by a shuffle-down Add22 tree.
+//
+// ff_gemv_t: one thread per pair of adjacent columns of A (coalesced
+// 16-byte loads along rows), one block row per row block of A.  Each thread
+// accumulates its rows in order; the row blocks' partial sums go to the
+// workspace and a second kernel adds them in row-block order.
+#include "ff_core.cuh"
+#include "ff_host.cuh"
+
+namespace {
+
+constexpr int kGBlock = 256;
+constexpr int kGWarps = kGBlock / 32;
+constexpr int kMaxK = 64;
+
+__device__ __forceinline__ float2 shfl_down2(float2 v, int off)
+{
+    return make_float2(__shfl_down_sync(0xffffffffu, v.x, off), __shfl_down_sync(0xffffffffu, v.y, off));
+}
+
+// ---------------------------------------------------------------------------
+// Y = A X
+// ---------------------------------------------------------------------------
+template <int KT, bool VEC>
+__global__ void __launch_bounds__(kGBlock)
+gemv_kernel(const float2* __restrict__ A, int64_t m, int64_t n, int64_t lda, const float2* __restrict__ X,
+            int64_t ldx, float2* __restrict__ Y, int64_t ldy)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t r = static_cast<int64_t>(blockIdx.x) * kGWarps + (threadIdx.x >> 5);
+    if (r >= m) return;
+    const float2* Ar = A + r * lda;
+    float2 acc[KT];
+#pragma unroll
+    for (int c = 0; c < KT; ++c) acc[c] = make_float2(0.0f, 0.0f);
+
+    if (VEC) {
+        // two columns per lane per step; n even, A rows and X columns 16-byte aligned
+        const float4* Ar4 = reinterpret_cast<const float4*>(Ar);
+        const int64_t n2 = n >> 1;
+        int64_t t = lane;
+        for (; t + 32 < n2; t += 64) {
+            const float4 a0 = __ldcs(Ar4 + t);
+            const float4 a1 = __ldcs(Ar4 + t + 32);
+#pragma unroll
+            for (int c = 0; c < KT; ++c) {
+                const float4* Xc = reinterpret_cast<const float4*>(X + c * ldx);
+                const float4 x0 = __ldg(Xc + t);
+                const float4 x1 = __ldg(Xc + t + 32);
+                acc[c] = ffk::add22(acc[c], ffk::mul22(make_float2(a0.x, a0.y), make_float2(x0.x, x0.y)));
+                acc[c] = ffk::add22(acc[c], ffk::mul22(make_float2(a0.z, a0.w), make_float2(x0.z, x0.w)));
+                acc[c] = ffk::add22(acc[c], ffk::mul22(make_float2(a1.x, a1.y), make_float2(x1.x, x1.y)));
+                acc[c] = ffk::add22(acc[c], ffk::mul22(make_float2(a1.z, a1.w), make_float2(x1.z, x1.w)));
+            }
+        }
+        for (; t < n2; t += 32) {
+            const float4 a0 = __ldcs(Ar4 + t);
+#pragma unroll
+            for (int c = 0; c < KT; ++c) {
+                const float4 x0 = __ldg(reinterpret_cast<const float4*>(X + c * ldx) + t);
+                acc[c] = ffk::add22(acc[c], ffk::mul22(make_float2(a0.x, a0.y), make_float2(x0.x, x0.y)));
+                acc[c] = ffk::add22(acc[c], ffk::mul22(make_float2(a0.z, a0.w), make_float2(x0.z, x0.w)));
+            }
+        }
+    } else {
+        for (int64_t j = lane; j < n; j += 32) {
+            const float2 a = Ar[j];
+#pragma unroll
+            for (int c = 0; c < KT; ++c) acc[c] = ffk::add22(acc[c], ffk::mul22(a, __ldg(X + c * ldx + j)));
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < KT; ++c) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc[c] = ffk::add22(acc[c], shfl_down2(acc[c], off));
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int c = 0; c < KT; ++c) Y[c * ldy + r] = acc[c];
+    }
+}
+
+template <int KT>
+ff_status launch_gemv_tile(const float2* A, int64_t m, int64_t n, int64_t lda, const float2* X, int64_t ldx,
+                           float2* Y, int64_t ldy, bool vec, cudaStream_t s)
+{
+    const unsigned grid = static_cast<unsigned>((m + kGWarps - 1) / kGWarps);
+    if (vec)
+        gemv_kernel<KT, true><<<grid, kGBlock, 0, s>>>(A, m, n, lda, X, ldx, Y, ldy);
+    else
+        gemv_kernel<KT, false><<<grid, kGBlock, 0, s>>>(A, m, n, lda, X, ldx, Y, ldy);
+    return ffh::check_launch();
+}
+
+// Largest supported tile width <= k.
+inline int tile_for(int64_t k) { return k >= 16 ? 16 : k >= 8 ? 8 : k >= 4 ? 4 : k >= 2 ? 2 : 1; }
+
+// ---------------------------------------------------------------------------
+// dX = A^T dY
+// ---------------------------------------------------------------------------
+// Partial sums: ws[(rb * k + c) * n + j] for row block rb.
+template <int KT, bool VEC>
+__global__ void __launch_bounds__(kGBlock)
+gemv_t_kernel(const float2* __restrict__ A, int64_t m, int64_t n, int64_t lda, const float2* __restrict__ dY,
+              int64_t lddy, int64_t rows_per_block, float2* __restrict__ out, int64_t out_ld, int64_t out_rb_stride)
+{
+    const int64_t r0 = static_cast<int64_t>(blockIdx.y) * rows_per_block;
+    int64_t r1 = r0 + rows_per_block;
+    if (r1 > m) r1 = m;
+    float2* o = out + static_cast<int64_t>(blockIdx.y) * out_rb_stride;
+    if (VEC) {
+        const int64_t jp = static_cast<int64_t>(blockIdx.x) * kGBlock + threadIdx.x;  // column pair
+        if (2 * jp >= n) return;
+        float2 acc0[KT], acc1[KT];
+#pragma unroll
+        for (int c = 0; c < KT; ++c) {
+            acc0[c] = make_float2(0.0f, 0.0f);
+            acc1[c] = make_float2(0.0f, 0.0f);
+        }
+        int64_t r = r0;
+        for (; r + 1 < r1; r += 2) {
+            const float4 a0 = __ldcs(reinterpret_cast<const float4*>(A + r * lda) + jp);
+            const float4 a1 = __ldcs(reinterpret_cast<const float4*>(A + (r + 1) * lda) + jp);
+#pragma unroll
+            for (int c = 0; c < KT; ++c) {
+                const float2 d0 = __ldg(dY + c * lddy + r);
+                const float2 d1 = __ldg(dY + c * lddy + r + 1);
+                acc0[c] = ffk::add22(acc0[c], ffk::mul22(make_float2(a0.x, a0.y), d0));
+                acc1[c] = ffk::add22(acc1[c], ffk::mul22(make_float2(a0.z, a0.w), d0));
+                acc0[c] = ffk::add22(acc0[c], ffk::mul22(make_float2(a1.x, a1.y), d1));
+                acc1[c] = ffk::add22(acc1[c], ffk::mul22(make_float2(a1.z, a1.w), d1));
+            }
+        }
+        for (; r < r1; ++r) {
+            const float4 a0 = __ldcs(reinterpret_cast<const float4*>(A + r * lda) + jp);
+#pragma unroll
+            for (int c = 0; c < KT; ++c) {
+                const float2 d0 = __ldg(dY + c * lddy + r);
+                acc0[c] = ffk::add22(acc0[c], ffk::mul22(make_float2(a0.x, a0.y), d0));
+                acc1[c] = ffk::add22(acc1[c], ffk::mul22(make_float2(a0.z, a0.w), d0));
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < KT; ++c) {
+            o[c * out_ld + 2 * jp] = acc0[c];
+            o[c * out_ld + 2 * jp + 1] = acc1[c];
+        }
+    } else {
+        const int64_t j = static_cast<int64_t>(blockIdx.x) * kGBlock + threadIdx.x;
+        if (j >= n) return;
+        float2 acc[KT];
+#pragma unroll
+        for (int c = 0; c < KT; ++c) acc[c] = make_float2(0.0f, 0.0f);
+        for (int64_t r = r0; r < r1; ++r) {
+            const float2 a = A[r * lda + j];
+#pragma unroll
+            for (int c = 0; c < KT; ++c) acc[c] = ffk::add22(acc[c], ffk::mul22(a, __ldg(dY + c * lddy + r)));
+        }
+#pragma unroll
+        for (int c = 0; c < KT; ++c) o[c * out_ld + j] = acc[c];
+    }
+}
+
+// dX[c, j] = ws[0][c][j] (+) ws[1][c][j] (+) ... in row-block order.
+__global__ void __launch_bounds__(kGBlock)
+gemv_t_combine(const float2* __restrict__ ws, int64_t n, int64_t k, int64_t nrb, float2* __restrict__ dX,
+               int64_t lddx)
+{
+    const int64_t idx = static_cast<int64_t>(blockIdx.x) * kGBlock + threadIdx.x;
+    if (idx >= n * k) return;
+    const int64_t c = idx / n, j = idx - c * n;
+    float2 acc = ws[c * n + j];
+    for (int64_t rb = 1; rb < nrb; ++rb) acc = ffk::add22(acc, ws[(rb * k + c) * n + j]);
+    dX[c * lddx + j] = acc;
+}
+
+template <int KT>
+void launch_gemv_t_tile(const float2* A, int64_t m, int64_t n, int64_t lda, const float2* dY, int64_t lddy,
+                        int64_t rows_per_block, int64_t nrb, float2* out, int64_t out_ld, int64_t out_rb_stride,
+                        bool vec, cudaStream_t s)
+{
+    if (vec) {
+        const int64_t pairs = n / 2;
+        dim3 grid(static_cast<unsigned>((pairs + kGBlock - 1) / kGBlock), static_cast<unsigned>(nrb));
+        gemv_t_kernel<KT, true><<<grid, kGBlock, 0, s>>>(A, m, n, lda, dY, lddy, rows_per_block, out, out_ld,
+                                                           out_rb_stride);
+    } else {
+        dim3 grid(static_cast<unsigned>((n + kGBlock - 1) / kGBlock), static_cast<unsigned>(nrb));
+        gemv_t_kernel<KT, false><<<grid, kGBlock, 0, s>>>(A, m, n, lda, dY, lddy, rows_per_block, out, out_ld,
+                                                            out_rb_stride);
+    }
+}
+
+// Number of row blocks for the adjoint: enough blocks to fill the GPU a few
+// times over, each row block at least 64 rows long.
+int64_t row_blocks(int64_t m, int64_t n, int sm_count)
+{
+    const int64_t col_blocks = (n / 2 + kGBlock - 1) / kGBlock;
+    int64_t want = (static_cast<int64_t>(sm_count) * 4 + col_blocks - 1) / (col_blocks > 0 ? col_blocks : 1);
+    if (want < 1) want = 1;
+    int64_t maxrb = m / 64;
+    if (maxrb < 1) maxrb = 1;
+    if (want > maxrb) want = maxrb;
+    if (want > 64) want = 64;
+    return want;
+}
+
+// ---------------------------------------------------------------------------
+// binary64 GEMV (one warp per row, fma accumulation, shuffle tree)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kGBlock)
+gemv_f64_kernel(const double* __restrict__ A, int64_t m, int64_t n, int64_t lda, const double* __restrict__ X,
+                int64_t ldx, int64_t k0, int kt, double* __restrict__ Y, int64_t ldy)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t r = static_cast<int64_t>(blockIdx.x) * kGWarps + (threadIdx.x >> 5);
+    if (r >= m) return;
+    double acc[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) acc[c] = 0.0;
+    const double* Ar = A + r * lda;
+    for (int64_t j = lane; j < n; j += 32) {
+        const double a = __ldcs(Ar + j);
+#pragma unroll
+        for (int c = 0; c < 16; ++c)
+            if (c < kt) acc[c] = __fma_rn(a, __ldg(X + (k0 + c) * ldx + j), acc[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc[c] = __dadd_rn(acc[c], __shfl_down_sync(0xffffffffu, acc[c], off));
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int c = 0; c < 16; ++c)
+            if (c < kt) Y[(k0 + c) * ldy + r] = acc[c];
+    }
+}
+
+bool bad_dims(int64_t m, int64_t n, int64_t k) { return m < 0 || n < 0 || k < 1 || k > kMaxK; }
+
+size_t gemv_t_ws(int64_t m, int64_t n, int64_t k, int sm_count)
+{
+    const int64_t nrb = row_blocks(m, n, sm_count);
+    if (nrb <= 1) return 16;
+    return static_cast<size_t>(nrb) * static_cast<size_t>(n) * static_cast<size_t>(k) * sizeof(float2);
+}
+
+}  // namespace
+
+extern "C" {
+
+ff_status ff_gemv(const ff2* A_, int64_t m, int64_t n, int64_t lda, const ff2* X_, int64_t ldx, int64_t k,
+                  ff2* Y_, int64_t ldy, cudaStream_t s)
+{
+    if (bad_dims(m, n, k) || lda < n || ldx < n || ldy < m) return FF_ERR_INVALID_ARG;
+    const size_t an = static_cast<size_t>(m) * static_cast<size_t>(n);
+    if (!ffh::ok_ptr(A_, an) || !ffh::ok_ptr(X_, static_cast<size_t>(n)) || !ffh::ok_ptr(Y_, static_cast<size_t>(m)))
+        return FF_ERR_INVALID_ARG;
+    if (m == 0) return FF_OK;
+    auto* A = reinterpret_cast<const float2*>(A_);
+    auto* X = reinterpret_cast<const float2*>(X_);
+    auto* Y = reinterpret_cast<float2*>(Y_);
+    const bool vec = (n % 2 == 0) && (lda % 2 == 0) && (ldx % 2 == 0) && ffh::aligned(A, 16) && ffh::aligned(X, 16);
+    for (int64_t c0 = 0; c0 < k;) {
+        const int kt = tile_for(k - c0);
+        ff_status st;
+        const float2* Xc = X + c0 * ldx;
+        float2* Yc = Y + c0 * ldy;
+        switch (kt) {
+        case 16: st = launch_gemv_tile<16>(A, m, n, lda, Xc, ldx, Yc, ldy, vec, s); break;
+        case 8: st = launch_gemv_tile<8>(A, m, n, lda, Xc, ldx, Yc, ldy, vec, s); break;
+        case 4: st = launch_gemv_tile<4>(A, m, n, lda, Xc, ldx, Yc, ldy, vec, s); break;
+        case 2: st = launch_gemv_tile<2>(A, m, n, lda, Xc, ldx, Yc, ldy, vec, s); break;
+        default: st = launch_gemv_tile<1>(A, m, n, lda, Xc, ldx, Yc, ldy, vec, s); break;
+        }
+        if (st != FF_OK) return st;
+        c0 += kt;
+    }
+    return FF_OK;
+}
+
+size_t ff_gemv_t_workspace_bytes(int64_t m, int64_t n, int64_t k)
+{
+    if (bad_dims(m, n, k)) return 0;
+    ffh::DeviceInfo di;
+    if (ffh::device_info(&di) != FF_OK) return 0;
+    return gemv_t_ws(m, n, k, di.sm_count);
+}
+
+ff_status ff_gemv_t(const ff2* A_, int64_t m, int64_t n, int64_t lda, const ff2* dY_, int64_t lddy, int64_t k,
+                    ff2* dX_, int64_t lddx, void* ws, size_t ws_bytes, cudaStream_t s)
+{
+    if (bad_dims(m, n, k) || lda < n || lddy < m || lddx < n) return FF_ERR_INVALID_ARG;
+    const size_t an = static_cast<size_t>(m) * static_cast<size_t>(n);
+    if (!ffh::ok_ptr(A_, an) || !ffh::ok_ptr(dY_, static_cast<size_t>(m)) || !ffh::ok_ptr(dX_, static_cast<size_t>(n)))
+        return FF_ERR_INVALID_ARG;
+    if (n == 0) return FF_OK;
+    ffh::DeviceInfo di;
+    ff_status st = ffh::device_info(&di);
+    if (st != FF_OK) return st;
+    auto* A = reinterpret_cast<const float2*>(A_);
+    auto* dY = reinterpret_cast<const float2*>(dY_);
+    auto* dX = reinterpret_cast<float2*>(dX_);
+    const int64_t nrb = row_blocks(m, n, di.sm_count);
+    const int64_t rpb = m > 0 ? (m + nrb - 1) / nrb : 0;
+    float2* part = nullptr;
+    if (nrb > 1) {
+        if (ws == nullptr || ws_bytes < gemv_t_ws(m, n, k, di.sm_count) || !ffh::aligned(ws, 16))
+            return FF_ERR_WORKSPACE;
+        part = static_cast<float2*>(ws);
+    }
+    const bool vec = (n % 2 == 0) && (lda % 2 == 0) && ffh::aligned(A, 16);
+    for (int64_t c0 = 0; c0 < k;) {
+        const int kt = tile_for(k - c0);
+        const float2* dYc = dY + c0 * lddy;
+        // one row block: write dX directly; else partials [rb][c][j]
+        float2* out = nrb > 1 ? part + c0 * n : dX + c0 * lddx;
+        const int64_t out_ld = nrb > 1 ? n : lddx;
+        const int64_t rb_stride = nrb > 1 ? k * n : 0;
+        const int64_t mm = m > 0 ? m : 0;
+        switch (kt) {
+        case 16: launch_gemv_t_tile<16>(A, mm, n, lda, dYc, lddy, rpb, nrb, out, out_ld, rb_stride, vec, s); break;
+        case 8: launch_gemv_t_tile<8>(A, mm, n, lda, dYc, lddy, rpb, nrb, out, out_ld, rb_stride, vec, s); break;
+        case 4: launch_gemv_t_tile<4>(A, mm, n, lda, dYc, lddy, rpb, nrb, out, out_ld, rb_stride, vec, s); break;
+        case 2: launch_gemv_t_tile<2>(A, mm, n, lda, dYc, lddy, rpb, nrb, out, out_ld, rb_stride, vec, s); break;
+        default: launch_gemv_t_tile<1>(A, mm, n, lda, dYc, lddy, rpb, nrb, out, out_ld, rb_stride, vec, s); break;
+        }
+        st = ffh::check_launch();
+        if (st != FF_OK) return st;
+        c0 += kt;
+    }
+    if (nrb > 1) {
+        const int64_t total = n * k;
+        gemv_t_combine<<<static_cast<unsigned>((total + kGBlock - 1) / kGBlock), kGBlock, 0, s>>>(part, n, k, nrb, dX,
+                                                                                                  lddx);
+        st = ffh::check_launch();
+        if (st != FF_OK) return st;
+    }
+    return FF_OK;
+}
+
+ff_status ff_f64_gemv(const double* A, int64_t m, int64_t n, int64_t lda, const double* X, int64_t ldx, int64_t k,
+                      double* Y, int64_t ldy, cudaStream_t s)
+{
+    if (bad_dims(m, n, k) || lda < n || ldx < n || ldy < m) return FF_ERR_INVALID_ARG;
+    const size_t an = static_cast<size_t>(m) * static_cast<size_t>(n);
+    if (!ffh::ok_ptr(A, an) || !ffh::ok_ptr(X, static_cast<size_t>(n)) || !ffh::ok_ptr(Y, static_cast<size_t>(m)))
+        return FF_ERR_INVALID_ARG;
+    if (m == 0) return FF_OK;
+    const unsigned grid = static_cast<unsigned>((m + kGWarps - 1) / kGWarps);
+    for (int64_t c0 = 0; c0 < k; c0 += 16) {
+        const int kt = static_cast<int>(k - c0 < 16 ? k - c0 : 16);
+        gemv_f64_kernel<<<grid, kGBlock, 0, s>>>(A, m, n, lda, X, ldx, c0, kt, Y, ldy);
+        ff_status st = ffh::check_launch();
+        if (st != FF_OK) return st;
+    }
+    return FF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,300 @@
+// ff_reduce.cu -- deterministic compensated reductions: the float-float sum
+// and dot product (Add22 accumulation of the paper's operators, the
+// "compensated algorithms" of Section 7) and a binary64 dot baseline.
+//
+// One launch per reduction.  Order of combination (fixed for a given n,
+// device and build, hence bit-reproducible):
+//   1. thread t of T = grid x 256 threads starts from zero and accumulates,
+//      left to right, the head element (thread 0 only, when the arrays are
+//      not 16-byte aligned), then the two-element chunks t, t + T, t + 2T, ...
+//      (element pair 2c, 2c+1 of chunk c, in that order), then the odd tail
+//      element (thread 0 only);
+//   2. each warp combines lanes with a shuffle-down tree
+//      (v_l = combine(v_l, v_{l+off}), off = 16, 8, 4, 2, 1);
+//   3. lane 0 of each warp stores its value; warp 0 combines the 8 warp
+//      values with the same tree (off = 4, 2, 1);
+//   4. every block stores its value in the workspace; the last block to
+//      arrive (atomic ticket) accumulates the block values b, b + 256, ... per
+//      thread, from zero, and reduces them with steps 2-3.
+// No block ever waits for another.
+#include "ff_core.cuh"
+#include "ff_host.cuh"
+
+namespace {
+
+constexpr int kRBlock = 256;
+constexpr int kRWarps = kRBlock / 32;
+constexpr int kRMaxBlocksPerSm = 8;
+constexpr size_t kPartialsOffset = 256;  // ticket at offset 0, partials at 256
+
+struct FFSum {
+    using T = float2;
+    using Acc = float2;
+    static constexpr bool kDot = false;
+    __device__ static Acc zero() { return make_float2(0.0f, 0.0f); }
+    __device__ static Acc step(Acc acc, T x, T) { return ffk::add22(acc, x); }
+    __device__ static Acc combine(Acc a, Acc b) { return ffk::add22(a, b); }
+    __device__ static Acc shfl_down(Acc v, int off)
+    {
+        return make_float2(__shfl_down_sync(0xffffffffu, v.x, off), __shfl_down_sync(0xffffffffu, v.y, off));
+    }
+};
+
+struct FFDot : FFSum {
+    static constexpr bool kDot = true;
+    __device__ static Acc step(Acc acc, T x, T y) { return ffk::add22(acc, ffk::mul22(x, y)); }
+};
+
+struct F64Dot {
+    using T = double;
+    using Acc = double;
+    static constexpr bool kDot = true;
+    __device__ static Acc zero() { return 0.0; }
+    __device__ static Acc step(Acc acc, T x, T y) { return __fma_rn(x, y, acc); }
+    __device__ static Acc combine(Acc a, Acc b) { return __dadd_rn(a, b); }
+    __device__ static Acc shfl_down(Acc v, int off) { return __shfl_down_sync(0xffffffffu, v, off); }
+};
+
+template <typename T> struct V16;
+template <> struct V16<float2> { using V = float4; };
+template <> struct V16<double> { using V = double2; };
+
+template <typename T>
+union Pack2 {
+    typename V16<T>::V v;
+    T e[2];
+};
+
+// Steps 2-3: the block's combined value ends in thread 0.
+template <class P>
+__device__ __forceinline__ typename P::Acc block_reduce(typename P::Acc v, typename P::Acc* sm)
+{
+    const int lane = threadIdx.x & 31;
+    const int w = threadIdx.x >> 5;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = P::combine(v, P::shfl_down(v, off));
+    if (lane == 0) sm[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        v = (lane < kRWarps) ? sm[lane] : P::zero();
+#pragma unroll
+        for (int off = kRWarps / 2; off > 0; off >>= 1) v = P::combine(v, P::shfl_down(v, off));
+    }
+    __syncthreads();
+    return v;
+}
+
+template <class P, int U>
+__global__ void __launch_bounds__(kRBlock)
+reduce_kernel(const typename P::T* x, const typename P::T* y, size_t n, int head, typename P::Acc* out,
+              typename P::Acc* partials, unsigned* ticket)
+{
+    using T = typename P::T;
+    using Acc = typename P::Acc;
+    using V = typename V16<T>::V;
+    __shared__ Acc sm[kRWarps];
+    __shared__ bool is_last;
+
+    const size_t tid = static_cast<size_t>(blockIdx.x) * kRBlock + threadIdx.x;
+    const size_t nthr = static_cast<size_t>(gridDim.x) * kRBlock;
+    const size_t h = static_cast<size_t>(head);
+    const size_t nv = (n - h) / 2;
+
+    Acc acc = P::zero();
+    if (tid == 0 && h == 1) acc = P::step(acc, x[0], P::kDot ? y[0] : T());
+
+    const V* xv = reinterpret_cast<const V*>(x + h);
+    const V* yv = reinterpret_cast<const V*>((P::kDot ? y : x) + h);
+    size_t i = tid;
+    for (; i + (U - 1) * nthr < nv; i += U * nthr) {
+        Pack2<T> xs[U], ys[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            xs[u].v = __ldcs(xv + i + u * nthr);
+            if (P::kDot) ys[u].v = __ldcs(yv + i + u * nthr);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            acc = P::step(acc, xs[u].e[0], P::kDot ? ys[u].e[0] : T());
+            acc = P::step(acc, xs[u].e[1], P::kDot ? ys[u].e[1] : T());
+        }
+    }
+    for (; i < nv; i += nthr) {
+        Pack2<T> xs, ys;
+        xs.v = __ldcs(xv + i);
+        if (P::kDot) ys.v = __ldcs(yv + i);
+        acc = P::step(acc, xs.e[0], P::kDot ? ys.e[0] : T());
+        acc = P::step(acc, xs.e[1], P::kDot ? ys.e[1] : T());
+    }
+    if (tid == 0 && ((n - h) & 1)) acc = P::step(acc, x[n - 1], P::kDot ? y[n - 1] : T());
+
+    acc = block_reduce<P>(acc, sm);
+    if (gridDim.x == 1) {
+        if (threadIdx.x == 0) *out = acc;
+        return;
+    }
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = acc;
+        __threadfence();
+        const unsigned t = atomicAdd(ticket, 1u);
+        is_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    Acc a2 = P::zero();
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += kRBlock) a2 = P::combine(a2, __ldcg(partials + b));
+    a2 = block_reduce<P>(a2, sm);
+    if (threadIdx.x == 0) {
+        *out = a2;
+        *ticket = 0u;
+    }
+}
+
+// Unaligned operands (offsets modulo 16 differ): scalar loads, same tree.
+template <class P>
+__global__ void __launch_bounds__(kRBlock)
+reduce_scalar_kernel(const typename P::T* x, const typename P::T* y, size_t n, typename P::Acc* out,
+                     typename P::Acc* partials, unsigned* ticket)
+{
+    using T = typename P::T;
+    using Acc = typename P::Acc;
+    __shared__ Acc sm[kRWarps];
+    __shared__ bool is_last;
+    const size_t tid = static_cast<size_t>(blockIdx.x) * kRBlock + threadIdx.x;
+    const size_t nthr = static_cast<size_t>(gridDim.x) * kRBlock;
+    Acc acc = P::zero();
+    for (size_t i = tid; i < n; i += nthr) acc = P::step(acc, x[i], P::kDot ? y[i] : T());
+    acc = block_reduce<P>(acc, sm);
+    if (gridDim.x == 1) {
+        if (threadIdx.x == 0) *out = acc;
+        return;
+    }
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = acc;
+        __threadfence();
+        const unsigned t = atomicAdd(ticket, 1u);
+        is_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    Acc a2 = P::zero();
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += kRBlock) a2 = P::combine(a2, __ldcg(partials + b));
+    a2 = block_reduce<P>(a2, sm);
+    if (threadIdx.x == 0) {
+        *out = a2;
+        *ticket = 0u;
+    }
+}
+
+constexpr int kU = 4;
+
+size_t max_blocks(const ffh::DeviceInfo& di) { return static_cast<size_t>(di.sm_count) * kRMaxBlocksPerSm; }
+
+size_t workspace_bytes(const ffh::DeviceInfo& di) { return kPartialsOffset + max_blocks(di) * 8; }
+
+struct Shape {
+    unsigned grid;
+    int head;
+    bool vec;
+};
+
+template <class P>
+Shape shape_for(const typename P::T* x, const typename P::T* y, size_t n, const ffh::DeviceInfo& di)
+{
+    using T = typename P::T;
+    const uintptr_t px = reinterpret_cast<uintptr_t>(x) & 15u;
+    const uintptr_t py = P::kDot ? (reinterpret_cast<uintptr_t>(y) & 15u) : px;
+    Shape sh{};
+    sh.vec = (px == py) && (px % sizeof(T) == 0);
+    const size_t cap = max_blocks(di);
+    if (sh.vec) {
+        sh.head = (px != 0 && n > 0) ? 1 : 0;
+        const void* kern = reinterpret_cast<const void*>(&reduce_kernel<P, kU>);
+        int occ = ffh::occupancy(kern, kRBlock);
+        if (occ > kRMaxBlocksPerSm) occ = kRMaxBlocksPerSm;
+        const size_t nv = n > static_cast<size_t>(sh.head) ? (n - sh.head) / 2 : 0;
+        sh.grid = ffh::grid_for(nv, static_cast<size_t>(kRBlock) * kU, di.sm_count, occ);
+    } else {
+        sh.head = 0;
+        const void* kern = reinterpret_cast<const void*>(&reduce_scalar_kernel<P>);
+        int occ = ffh::occupancy(kern, kRBlock);
+        if (occ > kRMaxBlocksPerSm) occ = kRMaxBlocksPerSm;
+        sh.grid = ffh::grid_for(n, static_cast<size_t>(kRBlock) * kU, di.sm_count, occ);
+    }
+    if (sh.grid > cap) sh.grid = static_cast<unsigned>(cap);
+    return sh;
+}
+
+template <class P>
+ff_status run_reduce(const typename P::T* x, const typename P::T* y, size_t n, typename P::Acc* out, void* ws,
+                     size_t ws_bytes, cudaStream_t s)
+{
+    using T = typename P::T;
+    if (!ffh::ok_ptr(x, n) || (P::kDot && !ffh::ok_ptr(y, n))) return FF_ERR_INVALID_ARG;
+    if (!ffh::ok_ptr(out, 1)) return FF_ERR_INVALID_ARG;
+    ffh::DeviceInfo di;
+    ff_status st = ffh::device_info(&di);
+    if (st != FF_OK) return st;
+    if (ws == nullptr || ws_bytes < workspace_bytes(di) || !ffh::aligned(ws, 16)) return FF_ERR_WORKSPACE;
+
+    unsigned* ticket = static_cast<unsigned*>(ws);
+    auto* partials = reinterpret_cast<typename P::Acc*>(static_cast<char*>(ws) + kPartialsOffset);
+    const Shape sh = shape_for<P>(x, y, n, di);
+    if (sh.grid > 1) {
+        st = ffh::cuda_status(cudaMemsetAsync(ticket, 0, sizeof(unsigned), s));
+        if (st != FF_OK) return st;
+    }
+    if (sh.vec)
+        reduce_kernel<P, kU><<<sh.grid, kRBlock, 0, s>>>(x, y, n, sh.head, out, partials, ticket);
+    else
+        reduce_scalar_kernel<P><<<sh.grid, kRBlock, 0, s>>>(x, y, n, out, partials, ticket);
+    return ffh::check_launch();
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t ff_reduce_workspace_bytes(size_t n)
+{
+    (void)n;
+    ffh::DeviceInfo di;
+    if (ffh::device_info(&di) != FF_OK) return kPartialsOffset + 1024 * 8 * 8;
+    return workspace_bytes(di);
+}
+
+ff_status ff_reduce_launch_shape(const ff2* x, const ff2* y, size_t n, unsigned* grid, int* head, int* vector)
+{
+    if (!grid || !head || !vector) return FF_ERR_INVALID_ARG;
+    ffh::DeviceInfo di;
+    ff_status st = ffh::device_info(&di);
+    if (st != FF_OK) return st;
+    Shape sh = y ? shape_for<FFDot>(reinterpret_cast<const float2*>(x), reinterpret_cast<const float2*>(y), n, di)
+                 : shape_for<FFSum>(reinterpret_cast<const float2*>(x), nullptr, n, di);
+    *grid = sh.grid;
+    *head = sh.head;
+    *vector = sh.vec ? 1 : 0;
+    return FF_OK;
+}
+
+ff_status ff_sum(const ff2* x, size_t n, ff2* out_dev, void* ws, size_t ws_bytes, cudaStream_t s)
+{
+    return run_reduce<FFSum>(reinterpret_cast<const float2*>(x), nullptr, n, reinterpret_cast<float2*>(out_dev), ws,
+                             ws_bytes, s);
+}
+
+ff_status ff_dot(const ff2* x, const ff2* y, size_t n, ff2* out_dev, void* ws, size_t ws_bytes, cudaStream_t s)
+{
+    return run_reduce<FFDot>(reinterpret_cast<const float2*>(x), reinterpret_cast<const float2*>(y), n,
+                             reinterpret_cast<float2*>(out_dev), ws, ws_bytes, s);
+}
+
+ff_status ff_f64_dot(const double* x, const double* y, size_t n, double* out_dev, void* ws, size_t ws_bytes,
+                     cudaStream_t s)
+{
+    return run_reduce<F64Dot>(x, y, n, out_dev, ws, ws_bytes, s);
+}
+
+}  // extern "C"

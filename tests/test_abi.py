@@ -1,0 +1,76 @@
+"""The C ABI library builds, loads and exports every symbol include/ff.h
+declares, and its host-side argument checks return status codes without
+touching a GPU.  No test here launches a kernel."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_cs_0603115_gb300 import build, _lib
+    build.build()
+    return _lib.load()
+
+
+def test_exports_every_declared_symbol(lib):
+    from paper_cs_0603115_gb300 import _lib
+    declared = _lib.declared_symbols()
+    assert len(declared) >= 25
+    missing = [s for s in declared if not hasattr(lib, s)]
+    assert not missing, missing
+    # the binding declares a signature for every entry point of the header
+    assert sorted(_lib.SIGNATURES) == declared
+
+
+def test_build_id_and_status_strings(lib):
+    assert len(lib.ff_build_id()) > 0
+    assert lib.ff_status_string(0) == b"FF_OK"
+    assert lib.ff_status_string(2) == b"FF_ERR_WORKSPACE"
+    err = ctypes.c_int(-1)
+    assert lib.ff_last_cuda_error(ctypes.byref(err)) == 0
+    assert lib.ff_last_cuda_error(None) == 1
+
+
+def test_invalid_arguments_rejected_on_host(lib):
+    INVALID = 1
+    good = 1 << 20          # never dereferenced: every call below fails its checks
+    mis = good + 4          # not 8-byte aligned
+    assert lib.ff_add(None, good, good, 10, None) == INVALID
+    assert lib.ff_add(good, good, None, 10, None) == INVALID
+    assert lib.ff_add(mis, good, good, 10, None) == INVALID
+    assert lib.ff_mul12(good, None, 5, None) == INVALID
+    assert lib.ff_sqrt(None, good, 1, None) == INVALID
+    assert lib.ff_dot(None, good, 3, good, good, 4096, None) == INVALID
+    assert lib.ff_sum(good, 3, None, good, 4096, None) == INVALID
+    assert lib.ff_dot_backward(good, None, good, good, good, 3, None) == INVALID
+    assert lib.ff_gemv(good, 4, 4, 3, good, 4, 1, good, 4, None) == INVALID   # lda < n
+    assert lib.ff_gemv(good, 4, 4, 4, good, 4, 0, good, 4, None) == INVALID   # k < 1
+    assert lib.ff_gemv(good, 4, 4, 4, good, 4, 65, good, 4, None) == INVALID  # k > 64
+    assert lib.ff_gemv(good, -1, 4, 4, good, 4, 1, good, 4, None) == INVALID
+    assert lib.ff_gemv_t(good, 4, 4, 4, good, 3, 1, good, 4, good, 1 << 20, None) == INVALID
+    assert lib.ff_f64_add(good, mis, good, 3, None) == INVALID
+
+
+def test_zero_length_is_a_host_noop(lib):
+    # n == 0: nothing to launch, no pointer needed
+    assert lib.ff_add(None, None, None, 0, None) == 0
+    assert lib.ff_add12(None, None, 0, None) == 0
+    assert lib.ff_f32_add(None, None, None, 0, None) == 0
+
+
+def test_product_never_imports_the_oracle():
+    pkg = os.path.join(ROOT, "paper_cs_0603115_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(import|from)\s+oracle\b", text, re.M), f
+                assert "orc_" not in text, f
+    # the C sources of the oracle and the CUDA library share no file
+    csrc = set(os.listdir(os.path.join(pkg, "csrc")))
+    assert not (csrc & set(os.listdir(os.path.join(ROOT, "oracle"))))

@@ -1,0 +1,297 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Elementwise operators must match the oracle bit for bit (NaN == NaN);
+reductions must match a replay of their documented order bit for bit and stay
+within n 2^-46 sum|x_i y_i| of the exact value; GEMV rows stay within the
+same bound.  Sizes span several tiles and ragged tails; edge cases cover
+empty input, one to three elements, misaligned and mixed-alignment arrays,
+in-place operation, signed zeros, subnormals and specials.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_cs_0603115_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+if torch.cuda.is_available():
+    import paper_cs_0603115_gb300 as ff
+    from paper_cs_0603115_gb300 import _lib
+
+DEV = "cuda"
+N0 = 1 << 20
+
+
+def same_bits(got, want):
+    got = np.ascontiguousarray(got, np.float32)
+    want = np.ascontiguousarray(want, np.float32)
+    assert got.shape == want.shape
+    nan = np.isnan(got) & np.isnan(want)
+    eq = (got.view(np.uint32) == want.view(np.uint32)) | nan
+    if not eq.all():
+        bad = np.argwhere(~eq)[:5]
+        raise AssertionError(f"{(~eq).sum()} mismatches, first at {bad.tolist()}: "
+                             f"got {got[tuple(bad[0])]} want {want[tuple(bad[0])]}")
+
+
+@pytest.fixture(scope="module")
+def cfg0():
+    e = inputs.elementwise(N0 + 3, inputs.seed_for(0, 0))
+    return e
+
+
+def gpu(t):
+    return t.to(DEV)
+
+
+# ---------------------------------------------------------------------------
+# elementwise, bit-exact
+# ---------------------------------------------------------------------------
+
+def test_add12_mul12_bitexact(cfg0):
+    ab = cfg0.ab
+    same_bits(ff.add12(gpu(ab)).cpu().numpy(), oracle.add12(ab.numpy()))
+    same_bits(ff.mul12(gpu(ab)).cpu().numpy(), oracle.mul12(ab.numpy()))
+
+
+@pytest.mark.parametrize("op", ["add", "mul", "div"])
+def test_binary_ops_bitexact(cfg0, op):
+    a, b = cfg0.a, cfg0.b
+    got = getattr(ff, op)(gpu(a), gpu(b)).cpu().numpy()
+    want = {"add": oracle.add22, "mul": oracle.mul22, "div": oracle.div22}[op](a.numpy(), b.numpy())
+    same_bits(got, want)
+
+
+def test_sqrt_bitexact(cfg0):
+    a = cfg0.a_sqrt
+    same_bits(ff.sqrt(gpu(a)).cpu().numpy(), oracle.sqrt22(a.numpy()))
+
+
+def test_axpy_and_dot_backward_bitexact(cfg0):
+    a, b = cfg0.a, cfg0.b
+    alpha = inputs.scalar_ff(99).numpy()
+    same_bits(ff.axpy(alpha, gpu(a), gpu(b)).cpu().numpy(), oracle.axpy(alpha, a.numpy(), b.numpy()))
+    dout = gpu(torch.from_numpy(alpha.copy()))
+    dx, dy = ff.dot_backward(dout, gpu(a), gpu(b))
+    wdx, wdy = oracle.dot_backward(alpha, a.numpy(), b.numpy())
+    same_bits(dx.cpu().numpy(), wdx)
+    same_bits(dy.cpu().numpy(), wdy)
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 3, 4, 5, 7, 257, 4099, 65537])
+@pytest.mark.parametrize("offset", [0, 1])
+def test_ragged_and_misaligned(cfg0, n, offset):
+    """Lengths around the vector width and arrays starting 8 bytes past a
+    16-byte boundary (one-element scalar head)."""
+    a = gpu(cfg0.a[: n + 1])[offset:offset + n]
+    b = gpu(cfg0.b[: n + 1])[offset:offset + n]
+    an, bn = a.cpu().numpy(), b.cpu().numpy()
+    same_bits(ff.add(a, b).cpu().numpy(), oracle.add22(an, bn))
+    same_bits(ff.mul(a, b).cpu().numpy(), oracle.mul22(an, bn))
+    same_bits(ff.div(a, b).cpu().numpy(), oracle.div22(an, bn))
+    asq = gpu(cfg0.a_sqrt[: n + 1])[offset:offset + n]
+    same_bits(ff.sqrt(asq).cpu().numpy(), oracle.sqrt22(asq.cpu().numpy()))
+
+
+def test_mixed_alignment_scalar_path(cfg0):
+    n = 10001
+    a = gpu(cfg0.a[: n + 1])
+    b = gpu(cfg0.b[: n + 1])
+    out = torch.empty((n + 1, 2), dtype=torch.float32, device=DEV)
+    # a aligned, b and out 8 bytes off: offsets modulo 16 differ
+    ff.add(a[:n], b[1:], out=out[1:])
+    same_bits(out[1:].cpu().numpy(), oracle.add22(cfg0.a[:n].numpy(), cfg0.b[1:n + 1].numpy()))
+
+
+def test_in_place(cfg0):
+    n = 12345
+    a = gpu(cfg0.a[:n]).clone()
+    b = gpu(cfg0.b[:n])
+    want = oracle.mul22(cfg0.a[:n].numpy(), cfg0.b[:n].numpy())
+    ff.mul(a, b, out=a)
+    same_bits(a.cpu().numpy(), want)
+
+
+def test_special_values():
+    f = np.float32
+    vals = [0.0, -0.0, 1.0, -1.0, 2.0 ** -149, -(2.0 ** -149), 2.0 ** -126, 3.0e-39, 1e38, -1e38,
+            np.inf, -np.inf, np.nan, 2.0 ** 100, 2.0 ** -100, 1.5, 3.0]
+    lo_vals = [0.0, -0.0, 2.0 ** -149, 1e-30, -1e-20]
+    a = np.array([(h, l) for h in vals for l in lo_vals], f)
+    A = np.repeat(a, len(a), axis=0)
+    B = np.tile(a, (len(a), 1))
+    for op, ref in (("add", oracle.add22), ("mul", oracle.mul22), ("div", oracle.div22)):
+        got = getattr(ff, op)(gpu(torch.from_numpy(A)), gpu(torch.from_numpy(B))).cpu().numpy()
+        same_bits(got, ref(A, B))
+    same_bits(ff.sqrt(gpu(torch.from_numpy(a))).cpu().numpy(), oracle.sqrt22(a))
+    ab = np.stack([A[:, 0], B[:, 0]], 1)
+    same_bits(ff.add12(gpu(torch.from_numpy(ab))).cpu().numpy(), oracle.add12(ab))
+    same_bits(ff.mul12(gpu(torch.from_numpy(ab))).cpu().numpy(), oracle.mul12(ab))
+
+
+def test_subnormal_results_not_flushed():
+    ab = np.array([[2.0 ** -140, 2.0 ** -149], [2.0 ** -70, 2.0 ** -70], [1e-20, 1e-20]], np.float32)
+    got = ff.add12(gpu(torch.from_numpy(ab))).cpu().numpy()
+    assert got[0, 0] != 0
+    got = ff.mul12(gpu(torch.from_numpy(ab))).cpu().numpy()
+    assert got[1, 0] == np.float32(2.0 ** -140)
+    same_bits(got, oracle.mul12(ab))
+
+
+# ---------------------------------------------------------------------------
+# reductions
+# ---------------------------------------------------------------------------
+
+def shape_of(x, y):
+    import ctypes
+    g, h, v = ctypes.c_uint(), ctypes.c_int(), ctypes.c_int()
+    _lib.call("ff_reduce_launch_shape", x.data_ptr(), None if y is None else y.data_ptr(), x.shape[0],
+              ctypes.byref(g), ctypes.byref(h), ctypes.byref(v))
+    return g.value, h.value, bool(v.value)
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 3, 1000, 4099, 300001])
+@pytest.mark.parametrize("offset", [0, 1])
+def test_dot_and_sum_replay_bitexact(cfg0, n, offset):
+    x = gpu(cfg0.a[: n + 1])[offset:offset + n]
+    y = gpu(cfg0.b[: n + 1])[offset:offset + n]
+    xn, yn = x.cpu().numpy(), y.cpu().numpy()
+    import replay
+    g, h, v = shape_of(x, y)
+    same_bits(ff.dot(x, y).cpu().numpy(), replay.reduce_replay(oracle.mul22(xn, yn), g, h, v))
+    g, h, v = shape_of(x, None)
+    same_bits(ff.sum(x).cpu().numpy(), replay.reduce_replay(xn, g, h, v))
+
+
+def test_dot_mixed_alignment_replay(cfg0):
+    n = 70001
+    x = gpu(cfg0.a[: n + 1])[:n]
+    y = gpu(cfg0.b[: n + 1])[1:]
+    import replay
+    g, h, v = shape_of(x, y)
+    assert not v
+    want = replay.reduce_replay(oracle.mul22(x.cpu().numpy(), y.cpu().numpy()), g, h, v)
+    same_bits(ff.dot(x, y).cpu().numpy(), want)
+
+
+@pytest.mark.parametrize("cond", [1e3, 1e6, 1e9, 1e12])
+def test_dot_ill_conditioned_within_bound(cond):
+    n = 1 << 22
+    g = inputs.ill_dot(n, cond, inputs.seed_for(2, int(np.log10(cond))))
+    x, y = gpu(g.x), gpu(g.y)
+    r = ff.dot(x, y).cpu().numpy()
+    s_hi, s_lo, A, E = oracle.exact_dot(g.x.numpy(), g.y.numpy(), r)
+    assert abs(E) <= n * 2.0 ** -46 * A
+    # tree order: far inside the bound in practice
+    assert abs(E) <= 64 * 2.0 ** -46 * A
+    # deterministic
+    same_bits(ff.dot(x, y).cpu().numpy(), r)
+
+
+def test_sum_of_ones_and_n0():
+    for n in (0, 1, 3, 1000, 1 << 20):
+        x = torch.zeros((n, 2), dtype=torch.float32, device=DEV)
+        x[:, 0] = 1.0
+        r = ff.sum(x).cpu().numpy()
+        assert r[0] == n and r[1] == 0
+
+
+def test_autograd_dot():
+    e = inputs.elementwise(50001, inputs.seed_for(2, 9))
+    x = gpu(e.a).requires_grad_(True)
+    y = gpu(e.b).requires_grad_(True)
+    d = ff.ffdot(x, y)
+    dout = inputs.scalar_ff(5)
+    d.backward(gpu(dout))
+    wdx, wdy = oracle.dot_backward(dout.numpy(), e.a.numpy(), e.b.numpy())
+    same_bits(x.grad.cpu().numpy(), wdx)
+    same_bits(y.grad.cpu().numpy(), wdy)
+
+
+# ---------------------------------------------------------------------------
+# GEMV
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("m,n,k", [(37, 129, 1), (64, 256, 3), (200, 1000, 17), (33, 66, 64), (8, 7, 2)])
+def test_gemv_within_bound(m, n, k):
+    gi = inputs.gemv(m, n, k, inputs.seed_for(4, m + n + k))
+    A, X, dY = gpu(gi.A), gpu(gi.X), gpu(gi.dY)
+    Y = ff.gemv(A, X).cpu().numpy()
+    An, Xn, dYn = gi.A.numpy(), gi.X.numpy(), gi.dY.numpy()
+    for c in range(k):
+        for r in range(0, m, max(1, m // 16)):
+            _, _, Aabs, E = oracle.exact_dot(An[r], Xn[c], Y[c, r])
+            assert abs(E) <= 64 * 2.0 ** -46 * Aabs + 1e-300
+    dX = ff.gemv_t(A, dY).cpu().numpy()
+    At = np.ascontiguousarray(An.transpose(1, 0, 2))
+    for c in range(k):
+        for j in range(0, n, max(1, n // 16)):
+            _, _, Aabs, E = oracle.exact_dot(At[j], dYn[c], dX[c, j])
+            assert abs(E) <= 64 * 2.0 ** -46 * Aabs + 1e-300
+
+
+def test_gemv_autograd():
+    gi = inputs.gemv(64, 96, 4, inputs.seed_for(4, 77))
+    A = gpu(gi.A)
+    X = gpu(gi.X).requires_grad_(True)
+    Y = ff.ffgemv(A, X)
+    dY = gpu(gi.dY)
+    Y.backward(dY)
+    want = ff.gemv_t(A, dY)
+    same_bits(X.grad.cpu().numpy(), want.cpu().numpy())
+
+
+# ---------------------------------------------------------------------------
+# native baselines
+# ---------------------------------------------------------------------------
+
+def test_f64_and_f32_baselines(cfg0):
+    a64 = inputs.ff_to_f64(cfg0.a).to(DEV)
+    b64 = inputs.ff_to_f64(cfg0.b).to(DEV)
+    assert torch.equal(ff.f64_add(a64, b64), a64 + b64)
+    assert torch.equal(ff.f64_mul(a64, b64), a64 * b64)
+    assert torch.equal(ff.f64_div(a64, b64), a64 / b64)
+    s = a64.abs()
+    assert torch.equal(ff.f64_sqrt(s), torch.sqrt(s))
+    d = ff.f64_dot(a64, b64).item()
+    ex = oracle.exact_dot(cfg0.a.numpy(), cfg0.b.numpy())
+    assert abs(d - ex[0]) <= a64.numel() * 2.0 ** -53 * ex[2]
+    a32 = gpu(cfg0.a[:, 0].contiguous())
+    b32 = gpu(cfg0.b[:, 0].contiguous())
+    c32 = gpu(cfg0.ab[:, 1].contiguous())
+    same_bits(ff.f32_add(a32, b32).cpu().numpy(), oracle.fp32_add(a32.cpu().numpy(), b32.cpu().numpy()))
+    same_bits(ff.f32_mul(a32, b32).cpu().numpy(), oracle.fp32_mul(a32.cpu().numpy(), b32.cpu().numpy()))
+    same_bits(ff.f32_mad(a32, b32, c32).cpu().numpy(),
+              oracle.fp32_mad(a32.cpu().numpy(), b32.cpu().numpy(), c32.cpu().numpy()))
+    gi = inputs.gemv(40, 100, 3, 5)
+    A64 = inputs.ff_to_f64(gi.A).to(DEV)
+    X64 = inputs.ff_to_f64(gi.X).to(DEV)
+    Y = ff.f64_gemv(A64, X64)
+    torch.testing.assert_close(Y, X64 @ A64.T, rtol=1e-13, atol=0)
+
+
+# ---------------------------------------------------------------------------
+# full size (2^28 values), sampled against the oracle
+# ---------------------------------------------------------------------------
+
+def test_full_size_sampled_bitexact():
+    n = 1 << 28
+    e = inputs.elementwise(n, inputs.seed_for(1, 0), device=DEV)
+    g = torch.Generator().manual_seed(1234)
+    idx = torch.cat([torch.arange(4096), torch.randint(0, n, (1 << 20,), generator=g),
+                     torch.arange(n - 4096, n)]).to(DEV)
+    take = lambda t: t[idx].cpu().numpy()
+    a, b, ab, asq = take(e.a), take(e.b), take(e.ab), take(e.a_sqrt)
+    out = torch.empty_like(e.a)
+    same_bits(take(ff.add12(e.ab, out=out)), oracle.add12(ab))
+    same_bits(take(ff.mul12(e.ab, out=out)), oracle.mul12(ab))
+    same_bits(take(ff.add(e.a, e.b, out=out)), oracle.add22(a, b))
+    same_bits(take(ff.mul(e.a, e.b, out=out)), oracle.mul22(a, b))
+    same_bits(take(ff.div(e.a, e.b, out=out)), oracle.div22(a, b))
+    same_bits(take(ff.sqrt(e.a_sqrt, out=out)), oracle.sqrt22(asq))
+    # divisor floor of the operators holds for the generated divisors
+    assert e.b[:, 0].abs().min().item() >= 2.0 ** -60
+    del out, e
+    torch.cuda.empty_cache()
