@@ -1,0 +1,483 @@
+"""Benchmark of the GB300 float-float library.
+
+Default workload (one "step"): the elementwise float-float operator set on
+N = 2^28 values (2 GiB per float-float array, far larger than L2): Add12 and
+Mul12 on packed binary32 pairs, then Add22, Mul22, Div22 and Sqrt22 on
+float-float arrays -- 6 x 2^28 float-float operator applications (ff-ops) per
+step, each one kernel launch of libff.so through its C ABI.
+
+Prints ONE JSON line (rank 0) with the whole-job throughput in ff-op/s, the
+roofline of the dominant kernel against the measured HBM copy bandwidth, the
+end-to-end rate through host buffers, the oracle timed on the host cores, the
+SM clocks seen during the timed region, and per-row measurements of the other
+hot-path rows (reductions and their adjoint, GEMV and its adjoint, native
+FP64/FP32 baselines on the same GPU).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--rows all|main]
+  python bench.py --impl reference      # the CPU oracle, same metric
+Multi-GPU (torchrun): every rank runs its own 2^28 batch (weak scaling);
+timing is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("float-float ops/s & HBM GB/s vs GB300 peak; batched dot+grad vs plain at ≤2^-44 rel")
+UNIT = "ff-op/s"
+N_ELEM = 1 << 28
+OPS = ["add12", "mul12", "add", "mul", "div", "sqrt"]
+# algorithmic HBM bytes per value: packed (a, b) in + (s, e) out = 16;
+# two float-float inputs + one output = 24; one input + one output = 16
+BYTES_PER_VALUE = {"add12": 16, "mul12": 16, "add": 24, "mul": 24, "div": 24, "sqrt": 16}
+WORKLOAD = "elementwise float-float operators on 2^28 values (Add12, Mul12 packed; Add22, Mul22, Div22, Sqrt22)"
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured", "sm_max_mhz": d.get("sm_max_mhz")}
+    return {"hbm_gbs": 6800.0, "source": "fallback", "sm_max_mhz": 2070.0}
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        time.sleep(0.25)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (timing only; no data-path collective)
+# ---------------------------------------------------------------------------
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def init_dist(ws, local):
+    import torch
+    import torch.distributed as dist
+    if ws > 1 and not dist.is_initialized():
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return dist if ws > 1 else None
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, value: float) -> float:
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+def make_step(ff, e, outs):
+    """One step: the six operators, each one launch; returns per-op closures."""
+    return {
+        "add12": lambda: ff.add12(e.ab, out=outs[0]),
+        "mul12": lambda: ff.mul12(e.ab, out=outs[1]),
+        "add": lambda: ff.add(e.a, e.b, out=outs[2]),
+        "mul": lambda: ff.mul(e.a, e.b, out=outs[3]),
+        "div": lambda: ff.div(e.a, e.b, out=outs[4]),
+        "sqrt": lambda: ff.sqrt(e.a_sqrt, out=outs[5]),
+    }
+
+
+def time_fn(torch, fn, reps: int, warm: int = 2) -> float:
+    """Mean seconds per call, CUDA events on the current stream."""
+    for _ in range(warm):
+        fn()
+    s = torch.cuda.current_stream()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(s)
+    for _ in range(reps):
+        fn()
+    ev1.record(s)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1) / 1e3 / reps
+
+
+def cpu_baseline(e_gpu, min_seconds: float = 10.0):
+    """The CPU oracle as it stands (single-threaded C) on the first 2^26
+    values of the same arrays, repeated until at least min_seconds."""
+    import oracle
+    n = 1 << 26
+    a = e_gpu.a[:n].cpu().numpy()
+    b = e_gpu.b[:n].cpu().numpy()
+    ab = e_gpu.ab[:n].cpu().numpy()
+    asq = e_gpu.a_sqrt[:n].cpu().numpy()
+    oracle.lib()
+    fns = [lambda: oracle.add12(ab), lambda: oracle.mul12(ab), lambda: oracle.add22(a, b),
+           lambda: oracle.mul22(a, b), lambda: oracle.div22(a, b), lambda: oracle.sqrt22(asq)]
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        for f in fns:
+            f()
+        reps += 1
+        if time.perf_counter() - t0 >= min_seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": reps * len(fns) * n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first 2^26 values of the same arrays, all six operators, {reps} pass(es), "
+                      f"{dt:.1f} s, single-threaded C oracle"}
+
+
+def traffic_for(kernel: str, build_id: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on this exact build (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    ent = d.get(kernel)
+    if not ent or ent.get("build_id") != build_id:
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+def run_gpu(args):
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = init_dist(ws, local)
+    import paper_cs_0603115_gb300 as ff
+    from paper_cs_0603115_gb300 import build as ffbuild
+    from paper_cs_0603115_gb300 import inputs
+    if rank == 0 or not os.path.exists(ffbuild.LIB_PATH):
+        ffbuild.build()
+    barrier(dist)
+    lib = ff.load()
+    build_id = lib.ff_build_id().decode()
+    peaks = load_peaks()
+    dev = torch.device("cuda", local)
+
+    n = N_ELEM
+    e = inputs.elementwise(n, inputs.seed_for(1, 16 * rank), device=dev)
+    outs = [torch.empty_like(e.a) for _ in OPS]
+    step = make_step(ff, e, outs)
+    torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        for op in OPS:
+            step[op]()
+    torch.cuda.synchronize()
+
+    s = torch.cuda.current_stream()
+    evs = {op: [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                for _ in range(args.steps)] for op in OPS}
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(dist)
+    torch.cuda.synchronize()
+    t0.record(s)
+    for k in range(args.steps):
+        for op in OPS:
+            a_, b_ = evs[op][k]
+            a_.record(s)
+            step[op]()
+            b_.record(s)
+    t1.record(s)
+    torch.cuda.synchronize()
+    barrier(dist)
+    clk = clocks.stop()
+    elapsed = t0.elapsed_time(t1) / 1e3
+    elapsed_max = max_over_ranks(dist, elapsed)
+    per_op = {op: sum(a_.elapsed_time(b_) for a_, b_ in evs[op]) / 1e3 / args.steps for op in OPS}
+    ffops_step = len(OPS) * n
+    value = ws * ffops_step * args.steps / elapsed_max
+
+    rows = {}
+    for op in OPS:
+        gbs = BYTES_PER_VALUE[op] * n / per_op[op] / 1e9
+        rows[op] = {"ms": round(per_op[op] * 1e3, 4), "GB/s": round(gbs, 1),
+                    "frac_hbm": round(gbs / peaks["hbm_gbs"], 4), "ff_op_s": n / per_op[op]}
+    dom = max(OPS, key=lambda o: per_op[o])
+    ach = BYTES_PER_VALUE[dom] * n / per_op[dom] / 1e9
+    kname = {"add12": "ff_add12", "mul12": "ff_mul12", "add": "ff_add", "mul": "ff_mul", "div": "ff_div",
+             "sqrt": "ff_sqrt"}[dom]
+    traffic = traffic_for(kname, build_id)
+    roofline = {"bound": "hbm", "achieved": round(ach, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": round(ach / peaks["hbm_gbs"], 4), "traffic": traffic, "kernel": kname,
+                "algorithmic_bytes_per_launch": BYTES_PER_VALUE[dom] * n,
+                "peak_source": peaks["source"] + " copy bandwidth"}
+
+    # end to end through host buffers: H2D of the step's inputs, the six C-ABI
+    # calls, D2H of every result, per step
+    e2e = None
+    if not args.no_e2e:
+        host_in = {k: torch.empty_like(getattr(e, k), device="cpu").pin_memory() for k in ("a", "b", "ab", "a_sqrt")}
+        for k, t in host_in.items():
+            t.copy_(getattr(e, k))
+        host_out = torch.empty_like(e.a, device="cpu").pin_memory()
+        dev_in = {k: torch.empty_like(getattr(e, k)) for k in host_in}
+        from types import SimpleNamespace
+        de = SimpleNamespace(**dev_in)
+        st2 = make_step(ff, de, outs)
+        e2e_steps = max(1, min(args.steps, 5))
+
+        def one_e2e():
+            for k, t in host_in.items():
+                dev_in[k].copy_(t, non_blocking=True)
+            for op in OPS:
+                st2[op]()
+                host_out.copy_(outs[OPS.index(op)], non_blocking=True)
+
+        one_e2e()
+        torch.cuda.synchronize()
+        barrier(dist)
+        c0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            one_e2e()
+        torch.cuda.synchronize()
+        e_el = max_over_ranks(dist, time.perf_counter() - c0)
+        h2d = sum(t.numel() * t.element_size() for t in host_in.values())
+        d2h = len(OPS) * host_out.numel() * host_out.element_size()
+        e2e = {"value": ws * ffops_step * e2e_steps / e_el, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "steps": e2e_steps, "host_buffers": "pinned"}
+        del host_in, host_out, dev_in, de, st2
+        torch.cuda.synchronize()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline(e)
+
+    if args.rows == "all":
+        del outs, step
+        rows.update(extra_rows(torch, ff, inputs, e, dev, peaks))
+    del e
+    torch.cuda.empty_cache()
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed_max / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_values": n, "ops_per_step": OPS,
+                   "l2": "inputs larger than L2 (2 GiB per array)", "seed": inputs.seed_for(1, 0)},
+        "hbm_gbs_step": round(sum(BYTES_PER_VALUE[o] for o in OPS) * n / (elapsed_max / args.steps) / 1e9, 1),
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": len(OPS) * args.steps, "clocks": clk, "build_id": build_id, "rows": rows,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def extra_rows(torch, ff, inputs, e, dev, peaks):
+    """Measurements of the other hot-path rows (each timed alone)."""
+    out = {}
+    hbm = peaks["hbm_gbs"]
+    n = e.a.shape[0]
+    # native baselines on the same values (FP64 holds hi + lo exactly)
+    a64 = inputs.ff_to_f64(e.a)
+    b64 = inputs.ff_to_f64(e.b)
+    o64 = torch.empty_like(a64)
+    for name, fn, nb in (("f64_add", lambda: ff.f64_add(a64, b64, out=o64), 24),
+                         ("f64_mul", lambda: ff.f64_mul(a64, b64, out=o64), 24),
+                         ("f64_div", lambda: ff.f64_div(a64, b64, out=o64), 24),
+                         ("f64_sqrt", lambda: ff.f64_sqrt(a64.abs(), out=o64), 16)):
+        t = time_fn(torch, fn, 5)
+        out[name] = {"ms": round(t * 1e3, 4), "GB/s": round(nb * n / t / 1e9, 1), "op_s": n / t}
+    del a64, b64, o64
+    a32, b32 = e.a[:, 0].contiguous(), e.b[:, 0].contiguous()
+    c32 = e.ab[:, 1].contiguous()
+    o32 = torch.empty_like(a32)
+    for name, fn, nb in (("f32_add", lambda: ff.f32_add(a32, b32, out=o32), 12),
+                         ("f32_mul", lambda: ff.f32_mul(a32, b32, out=o32), 12),
+                         ("f32_mad", lambda: ff.f32_mad(a32, b32, c32, out=o32), 16)):
+        t = time_fn(torch, fn, 5)
+        out[name] = {"ms": round(t * 1e3, 4), "GB/s": round(nb * n / t / 1e9, 1), "op_s": n / t}
+    del a32, b32, c32, o32
+    torch.cuda.empty_cache()
+
+    # reductions and the dot adjoint on the ill-conditioned dot, n = 2^26
+    nd = 1 << 26
+    g = inputs.ill_dot(nd, 1e12, inputs.seed_for(2, 12), device=dev)
+    x, y = g.x, g.y
+    t = time_fn(torch, lambda: ff.dot(x, y), 10)
+    out["dot_2^26"] = {"ms": round(t * 1e3, 4), "GB/s": round(16 * nd / t / 1e9, 1),
+                       "frac_hbm": round(16 * nd / t / 1e9 / hbm, 4), "ff_op_s": 2 * nd / t}
+    t = time_fn(torch, lambda: ff.sum(x), 10)
+    out["sum_2^26"] = {"ms": round(t * 1e3, 4), "GB/s": round(8 * nd / t / 1e9, 1),
+                       "frac_hbm": round(8 * nd / t / 1e9 / hbm, 4), "ff_op_s": nd / t}
+    dout = torch.tensor([1.0, 0.0], device=dev)
+    dx = torch.empty_like(x)
+    dy = torch.empty_like(y)
+    t = time_fn(torch, lambda: ff.dot_backward(dout, x, y, dx, dy), 10)
+    out["dot_backward_2^26"] = {"ms": round(t * 1e3, 4), "GB/s": round(32 * nd / t / 1e9, 1),
+                                "frac_hbm": round(32 * nd / t / 1e9 / hbm, 4), "ff_op_s": 2 * nd / t}
+    x64, y64 = inputs.ff_to_f64(x), inputs.ff_to_f64(y)
+    t = time_fn(torch, lambda: ff.f64_dot(x64, y64), 10)
+    out["f64_dot_2^26"] = {"ms": round(t * 1e3, 4), "GB/s": round(16 * nd / t / 1e9, 1)}
+    del g, x, y, dx, dy, x64, y64
+    torch.cuda.empty_cache()
+
+    # GEMV and adjoint, A 32768 x 32768 (8 GiB), the 16 right-hand-side widths
+    M = N = 32768
+    ks = [1, 2, 3, 4, 5, 6, 8, 10, 12, 16, 20, 24, 32, 40, 48, 64]
+    gi = inputs.gemv(M, N, 1, inputs.seed_for(4, 0), device=dev)
+    A = gi.A
+    del gi
+    Xall = inputs.to_ff(inputs.loguniform_f64(64 * N, torch.Generator(device=dev).manual_seed(inputs.seed_for(4, 1)),
+                                              dev)).reshape(64, N, 2)
+    gem = {}
+    tot_f = tot_b = 0.0
+    for k in ks:
+        X = Xall[:k].contiguous()
+        tf = time_fn(torch, lambda: ff.gemv(A, X), 2, warm=1)
+        tb = time_fn(torch, lambda: ff.gemv_t(A, X), 2, warm=1)
+        tot_f += tf
+        tot_b += tb
+        gem[str(k)] = {"fwd_ms": round(tf * 1e3, 3), "adj_ms": round(tb * 1e3, 3),
+                       "fwd_ff_op_s": 2 * M * N * k / tf, "adj_ff_op_s": 2 * M * N * k / tb}
+    out["gemv_32768^2"] = {"per_k": gem, "sweep_fwd_ms": round(tot_f * 1e3, 2), "sweep_adj_ms": round(tot_b * 1e3, 2),
+                           "k1_fwd_GB/s": round(8 * M * N / (gem["1"]["fwd_ms"] / 1e3) / 1e9, 1)}
+    A64 = inputs.ff_to_f64(A)
+    del A
+    torch.cuda.empty_cache()
+    X64 = inputs.ff_to_f64(Xall)
+    f64 = {}
+    for k in (1, 16, 64):
+        X = X64[:k].contiguous()
+        t = time_fn(torch, lambda: ff.f64_gemv(A64, X), 1, warm=1)
+        f64[str(k)] = {"ms": round(t * 1e3, 3)}
+    out["f64_gemv_32768^2"] = f64
+    del A64, X64, Xall
+    torch.cuda.empty_cache()
+    return out
+
+
+# ---------------------------------------------------------------------------
+# the reference arm: the CPU oracle, same metric
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_cs_0603115_gb300 import inputs
+    oracle.build()
+    n = 1 << 22
+    e = inputs.elementwise(n, inputs.seed_for(1, 0))
+    a, b, ab, asq = (t.numpy() for t in (e.a, e.b, e.ab, e.a_sqrt))
+    fns = [lambda: oracle.add12(ab), lambda: oracle.mul12(ab), lambda: oracle.add22(a, b),
+           lambda: oracle.mul22(a, b), lambda: oracle.div22(a, b), lambda: oracle.sqrt22(asq)]
+    for _ in range(args.warmup):
+        for f in fns:
+            f()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for f in fns:
+            f()
+    dt = time.perf_counter() - t0
+    value = len(fns) * n * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_values": N_ELEM, "ops_per_step": OPS,
+                   "sample_per_step": "2^22 values of the same generator (the full 2^28 per step would take "
+                                      "minutes on one core)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"2^22 values per operator per step, {args.steps} steps"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=100)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    p.add_argument("--rows", choices=["all", "main"], default="all")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    args = p.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()
