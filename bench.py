@@ -461,6 +461,37 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_case(args):
+    """Profiling case: generate n values, run one operator `reps` times, exit.
+    Used to capture one kernel under ncu on a small input (no JSON line)."""
+    import torch
+    import paper_cs_0603115_gb300 as ff
+    from paper_cs_0603115_gb300 import build as ffbuild
+    from paper_cs_0603115_gb300 import inputs
+    ffbuild.build()
+    dev = torch.device("cuda", 0)
+    n = args.n
+    if args.case in ("dot", "sum", "dot_backward"):
+        g = inputs.ill_dot(n, 1e12, inputs.seed_for(2, 12), device=dev)
+        x, y = g.x, g.y
+        dout = torch.tensor([1.0, 0.0], device=dev)
+        fn = {"dot": lambda: ff.dot(x, y), "sum": lambda: ff.sum(x),
+              "dot_backward": lambda: ff.dot_backward(dout, x, y)}[args.case]
+    elif args.case in ("gemv", "gemv_t"):
+        m = int(math.isqrt(n))
+        gi = inputs.gemv(m, m, args.k, inputs.seed_for(4, 0), device=dev)
+        fn = (lambda: ff.gemv(gi.A, gi.X)) if args.case == "gemv" else (lambda: ff.gemv_t(gi.A, gi.dY))
+    else:
+        e = inputs.elementwise(n, inputs.seed_for(1, 0), device=dev)
+        outs = [torch.empty_like(e.a) for _ in OPS]
+        fn = make_step(ff, e, outs)[args.case]
+    torch.cuda.synchronize()
+    for _ in range(args.reps):
+        fn()
+    torch.cuda.synchronize()
+    print(f"case {args.case} n={n} reps={args.reps} ok")
+
+
 def main():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -470,7 +501,14 @@ def main():
     p.add_argument("--rows", choices=["all", "main"], default="all")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--case", default=None, help="profiling case: one operator on --n values, --reps launches")
+    p.add_argument("--n", type=int, default=1 << 24)
+    p.add_argument("--k", type=int, default=1)
+    p.add_argument("--reps", type=int, default=3)
     args = p.parse_args()
+    if args.case:
+        run_case(args)
+        return
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
