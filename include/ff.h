@@ -171,6 +171,87 @@ FF_API ff_status ff_gemv_t(const ff2* A, int64_t m, int64_t n, int64_t lda, cons
                     cudaStream_t s);
 
 /* ------------------------------------------------------------------------ */
+/* Batched dot / AXPY: many instances in one persistent launch               */
+/* ------------------------------------------------------------------------ */
+
+typedef enum ff_batch_kind { FF_BATCH_DOT = 0, FF_BATCH_AXPY = 1 } ff_batch_kind;
+
+/* One instance.  DOT: *out = sum_i Mul22(x[i], y[i]) (out: one ff2 on the
+ * device), with the Add22 accumulation of ff_dot.  AXPY: out[i] =
+ * Add22(Mul22(alpha, x[i]), y[i]) for i < n (out: n values), bit-identical to
+ * ff_axpy.  All pointers are device pointers owned by the caller and must
+ * stay valid while any plan or graph built from the instance is used. */
+typedef struct ff_batch_instance {
+    int32_t kind;
+    int32_t reserved;
+    int64_t n;
+    const ff2* x;
+    const ff2* y;
+    ff2* out;
+    ff2 alpha;
+} ff_batch_instance;
+
+/* Launch configuration of the batched kernel: threads per block (128, 256
+ * or 512), values per thread per tile (pairs_per_thread: 8 .. 128, tile =
+ * block x pairs_per_thread values) and resident blocks per SM (0 = as many
+ * as fit). */
+typedef struct ff_tune {
+    int32_t block;
+    int32_t pairs_per_thread;
+    int32_t blocks_per_sm;
+} ff_tune;
+
+typedef struct ff_batch_plan ff_batch_plan;
+typedef struct ff_batch_graph ff_batch_graph;
+
+/* Build a plan on the current device: cut every instance into tiles and copy
+ * the instance records and the tile list to device memory the plan owns
+ * (the only allocation of the library, made here, never in a run).
+ * tune_or_null == NULL uses {256, 32, 0}.  Unsupported tunes return
+ * FF_ERR_INVALID_ARG. */
+FF_API ff_status ff_batch_plan_create(const ff_batch_instance* inst, int count, const ff_tune* tune_or_null,
+                                      ff_batch_plan** out);
+
+/* Workspace bytes ff_batch_run needs for this plan. */
+FF_API size_t ff_batch_workspace_bytes(const ff_batch_plan* plan);
+
+/* The plan's tune, tile count and grid (any pointer may be NULL). */
+FF_API ff_status ff_batch_plan_info(const ff_batch_plan* plan, ff_tune* tune, int64_t* ntiles, unsigned* grid);
+
+/* Run every instance of the plan: one memset of the per-instance counters and
+ * one persistent kernel launch on stream s.  Graph-capturable. */
+FF_API ff_status ff_batch_run(const ff_batch_plan* plan, void* ws, size_t ws_bytes, cudaStream_t s);
+
+/* Free the plan's device and host memory (NULL is a no-op).  The caller must
+ * make sure no run of it is still executing. */
+FF_API void ff_batch_plan_destroy(ff_batch_plan* plan);
+
+/* Capture ff_batch_run(plan, ws) into a CUDA graph (on a private stream)
+ * and instantiate it. */
+FF_API ff_status ff_batch_graph_create(const ff_batch_plan* plan, void* ws, size_t ws_bytes,
+                                       ff_batch_graph** out);
+
+/* Launch the instantiated graph on stream s. */
+FF_API ff_status ff_batch_graph_launch(ff_batch_graph* g, cudaStream_t s);
+
+/* Destroy the graph (NULL is a no-op). */
+FF_API void ff_batch_graph_destroy(ff_batch_graph* g);
+
+/* The autotuner's candidate tunes: writes up to max of them to out (out may
+ * be NULL) and returns how many there are. */
+FF_API int ff_batch_tune_candidates(ff_tune* out, int max);
+
+/* Workspace bytes that suffice for ff_batch_autotune on these instances. */
+FF_API size_t ff_batch_autotune_workspace_bytes(const ff_batch_instance* inst, int count);
+
+/* Time every candidate tune on these instances (one warm-up run, then reps
+ * runs each, CUDA events on stream s; the instances' outputs are
+ * overwritten) and return the fastest in *best and its mean time per run in
+ * *best_ms (may be NULL).  Synchronises with stream s. */
+FF_API ff_status ff_batch_autotune(const ff_batch_instance* inst, int count, void* ws, size_t ws_bytes,
+                                   cudaStream_t s, int reps, ff_tune* best, float* best_ms);
+
+/* ------------------------------------------------------------------------ */
 /* Native baselines on the same GPU (measurement only)                       */
 /* ------------------------------------------------------------------------ */
 

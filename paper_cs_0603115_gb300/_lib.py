@@ -20,6 +20,15 @@ class ff2(ctypes.Structure):
     _fields_ = [("hi", ctypes.c_float), ("lo", ctypes.c_float)]
 
 
+class ff_batch_instance(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("reserved", ctypes.c_int32), ("n", ctypes.c_int64),
+                ("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("out", ctypes.c_void_p), ("alpha", ff2)]
+
+
+class ff_tune(ctypes.Structure):
+    _fields_ = [("block", ctypes.c_int32), ("pairs_per_thread", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32)]
+
+
 P = ctypes.c_void_p
 SZ = ctypes.c_size_t
 I64 = ctypes.c_int64
@@ -51,6 +60,17 @@ SIGNATURES = {
     "ff_f32_add": (ST, [P, P, P, SZ, P]),
     "ff_f32_mul": (ST, [P, P, P, SZ, P]),
     "ff_f32_mad": (ST, [P, P, P, P, SZ, P]),
+    "ff_batch_plan_create": (ST, [P, ctypes.c_int, P, ctypes.POINTER(ctypes.c_void_p)]),
+    "ff_batch_workspace_bytes": (SZ, [P]),
+    "ff_batch_plan_info": (ST, [P, P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_uint)]),
+    "ff_batch_run": (ST, [P, P, SZ, P]),
+    "ff_batch_plan_destroy": (None, [P]),
+    "ff_batch_graph_create": (ST, [P, P, SZ, ctypes.POINTER(ctypes.c_void_p)]),
+    "ff_batch_graph_launch": (ST, [P, P]),
+    "ff_batch_graph_destroy": (None, [P]),
+    "ff_batch_tune_candidates": (ctypes.c_int, [P, ctypes.c_int]),
+    "ff_batch_autotune_workspace_bytes": (SZ, [P, ctypes.c_int]),
+    "ff_batch_autotune": (ST, [P, ctypes.c_int, P, SZ, P, ctypes.c_int, P, ctypes.POINTER(ctypes.c_float)]),
     "ff_status_string": (ctypes.c_char_p, [ST]),
     "ff_last_cuda_error": (ST, [ctypes.POINTER(ctypes.c_int)]),
     "ff_build_id": (ctypes.c_char_p, []),

@@ -1,0 +1,498 @@
+// ff_batch.cu -- many independent float-float dot and AXPY instances of
+// uneven lengths in one persistent launch, a CUDA-graph wrapper around it,
+// and the autotuner that picks its block size, values per thread and
+// resident blocks per SM.
+//
+// Plan (host, once): every instance is cut into tiles of block x ppt values;
+// the tiles of all instances form one list, instance after instance.  The
+// plan copies the instance records and the tile list to device memory it
+// owns.
+//
+// Run: a persistent grid of (SMs x blocks per SM) blocks walks the tile list
+// round robin (block b takes tiles b, b + G, b + 2G, ...).
+//   AXPY tile: z_i = Add22(Mul22(alpha, x_i), y_i) for the tile's values.
+//   dot tile:  each thread accumulates its values left to right with
+//              Add22(acc, Mul22(x_i, y_i)); the block combines threads with
+//              the shuffle-down Add22 tree of ff_dot and stores the tile's
+//              partial; the tile that finishes its instance last (atomic
+//              counter per instance) adds the instance's tile partials in
+//              tile order and writes the result.
+// No block waits for another; the per-instance counters are zeroed by a
+// memset at the start of every run (and left zero by the last tile).
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "ff_core.cuh"
+#include "ff_host.cuh"
+
+struct DevInst {
+    const float2* x;
+    const float2* y;
+    float2* out;
+    float2 alpha;
+    int64_t n;
+    int64_t first_tile;
+    int32_t ntiles;
+    int32_t kind;
+    int32_t vec;
+    int32_t pad;
+};
+
+struct Tile {
+    int32_t inst;
+    int32_t pad;
+    int64_t start;
+};
+
+struct ff_batch_plan {
+    int count;
+    ff_tune tune;
+    int64_t ntiles;
+    int64_t ndot;
+    int64_t total_values;
+    int device;
+    unsigned grid;
+    DevInst* d_inst;
+    Tile* d_tiles;
+};
+
+struct ff_batch_graph {
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+};
+
+namespace {
+
+constexpr size_t kCountersAlign = 256;
+
+__device__ __forceinline__ float2 shfl_down2(float2 v, int off)
+{
+    return make_float2(__shfl_down_sync(0xffffffffu, v.x, off), __shfl_down_sync(0xffffffffu, v.y, off));
+}
+
+template <int BLOCK>
+__device__ __forceinline__ float2 block_reduce(float2 v, float2* sm)
+{
+    constexpr int W = BLOCK / 32;
+    const int lane = threadIdx.x & 31;
+    const int w = threadIdx.x >> 5;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = ffk::add22(v, shfl_down2(v, off));
+    if (lane == 0) sm[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        v = (lane < W) ? sm[lane] : make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int off = W / 2; off > 0; off >>= 1) v = ffk::add22(v, shfl_down2(v, off));
+    }
+    __syncthreads();
+    return v;
+}
+
+// PPT values per thread per tile (even).  Values of a tile are visited as
+// two-value chunks c = threadIdx.x + j * BLOCK, j = 0 .. PPT/2 - 1.
+template <int BLOCK, int PPT>
+__global__ void __launch_bounds__(BLOCK)
+batch_kernel(const DevInst* __restrict__ insts, const Tile* __restrict__ tiles, int64_t ntiles,
+             float2* __restrict__ partials, unsigned* __restrict__ counters)
+{
+    __shared__ float2 sm[BLOCK / 32];
+    __shared__ int is_last;
+    constexpr int CH = PPT / 2;   // chunks per thread per tile
+    constexpr int U = CH < 4 ? CH : 4;
+
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const Tile tl = tiles[t];
+        const DevInst I = insts[tl.inst];
+        const int64_t s0 = tl.start;
+        const int64_t s1 = min(s0 + static_cast<int64_t>(BLOCK) * PPT, I.n);
+        if (I.kind == FF_BATCH_DOT) {
+            float2 acc = make_float2(0.0f, 0.0f);
+            if (I.vec) {
+                const float4* xv = reinterpret_cast<const float4*>(I.x + s0);
+                const float4* yv = reinterpret_cast<const float4*>(I.y + s0);
+                const int64_t len = s1 - s0;
+                const int64_t nch = len >> 1;
+#pragma unroll 1
+                for (int j0 = 0; j0 < CH; j0 += U) {
+                    float4 xs[U], ys[U];
+                    bool ok[U];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const int64_t c = threadIdx.x + static_cast<int64_t>(j0 + u) * BLOCK;
+                        ok[u] = c < nch;
+                        if (ok[u]) {
+                            xs[u] = __ldcs(xv + c);
+                            ys[u] = __ldcs(yv + c);
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        if (ok[u]) {
+                            acc = ffk::add22(acc, ffk::mul22(make_float2(xs[u].x, xs[u].y), make_float2(ys[u].x, ys[u].y)));
+                            acc = ffk::add22(acc, ffk::mul22(make_float2(xs[u].z, xs[u].w), make_float2(ys[u].z, ys[u].w)));
+                        }
+                    }
+                }
+                if ((len & 1) && threadIdx.x == 0) acc = ffk::add22(acc, ffk::mul22(I.x[s1 - 1], I.y[s1 - 1]));
+            } else {
+                for (int j = 0; j < PPT; ++j) {
+                    const int64_t i = s0 + threadIdx.x + static_cast<int64_t>(j) * BLOCK;
+                    if (i < s1) acc = ffk::add22(acc, ffk::mul22(I.x[i], I.y[i]));
+                }
+            }
+            acc = block_reduce<BLOCK>(acc, sm);
+            if (I.ntiles == 1) {
+                if (threadIdx.x == 0) *I.out = acc;
+            } else {
+                if (threadIdx.x == 0) {
+                    partials[t] = acc;
+                    __threadfence();
+                    const unsigned old = atomicAdd(counters + tl.inst, 1u);
+                    is_last = (old == static_cast<unsigned>(I.ntiles) - 1u);
+                }
+                __syncthreads();
+                if (is_last) {
+                    __threadfence();
+                    float2 a2 = make_float2(0.0f, 0.0f);
+                    for (int p = threadIdx.x; p < I.ntiles; p += BLOCK)
+                        a2 = ffk::add22(a2, __ldcg(partials + I.first_tile + p));
+                    a2 = block_reduce<BLOCK>(a2, sm);
+                    if (threadIdx.x == 0) {
+                        *I.out = a2;
+                        counters[tl.inst] = 0u;
+                    }
+                }
+                __syncthreads();
+            }
+        } else {
+            const float2 al = I.alpha;
+            if (I.vec) {
+                const float4* xv = reinterpret_cast<const float4*>(I.x + s0);
+                const float4* yv = reinterpret_cast<const float4*>(I.y + s0);
+                float4* zv = reinterpret_cast<float4*>(I.out + s0);
+                const int64_t len = s1 - s0;
+                const int64_t nch = len >> 1;
+#pragma unroll 1
+                for (int j0 = 0; j0 < CH; j0 += U) {
+                    float4 xs[U], ys[U];
+                    bool ok[U];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const int64_t c = threadIdx.x + static_cast<int64_t>(j0 + u) * BLOCK;
+                        ok[u] = c < nch;
+                        if (ok[u]) {
+                            xs[u] = __ldcs(xv + c);
+                            ys[u] = __ldcs(yv + c);
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        if (ok[u]) {
+                            const int64_t c = threadIdx.x + static_cast<int64_t>(j0 + u) * BLOCK;
+                            const float2 r0 = ffk::add22(ffk::mul22(al, make_float2(xs[u].x, xs[u].y)),
+                                                         make_float2(ys[u].x, ys[u].y));
+                            const float2 r1 = ffk::add22(ffk::mul22(al, make_float2(xs[u].z, xs[u].w)),
+                                                         make_float2(ys[u].z, ys[u].w));
+                            __stcs(zv + c, make_float4(r0.x, r0.y, r1.x, r1.y));
+                        }
+                    }
+                }
+                if ((len & 1) && threadIdx.x == 0)
+                    I.out[s1 - 1] = ffk::add22(ffk::mul22(al, I.x[s1 - 1]), I.y[s1 - 1]);
+            } else {
+                for (int j = 0; j < PPT; ++j) {
+                    const int64_t i = s0 + threadIdx.x + static_cast<int64_t>(j) * BLOCK;
+                    if (i < s1) I.out[i] = ffk::add22(ffk::mul22(al, I.x[i]), I.y[i]);
+                }
+            }
+        }
+    }
+}
+
+using KernelFn = void (*)(const DevInst*, const Tile*, int64_t, float2*, unsigned*);
+
+struct Variant {
+    int block;
+    int ppt;
+    KernelFn fn;
+};
+
+const Variant kVariants[] = {
+    {128, 16, batch_kernel<128, 16>}, {128, 32, batch_kernel<128, 32>}, {128, 64, batch_kernel<128, 64>},
+    {128, 128, batch_kernel<128, 128>}, {256, 8, batch_kernel<256, 8>}, {256, 16, batch_kernel<256, 16>},
+    {256, 32, batch_kernel<256, 32>}, {256, 64, batch_kernel<256, 64>}, {256, 128, batch_kernel<256, 128>},
+    {512, 8, batch_kernel<512, 8>}, {512, 16, batch_kernel<512, 16>}, {512, 32, batch_kernel<512, 32>},
+    {512, 64, batch_kernel<512, 64>},
+};
+
+const Variant* find_variant(int block, int ppt)
+{
+    for (const Variant& v : kVariants)
+        if (v.block == block && v.ppt == ppt) return &v;
+    return nullptr;
+}
+
+const ff_tune kDefaultTune = {256, 32, 0};
+
+size_t ws_bytes_for(const ff_batch_plan* p)
+{
+    const size_t counters = ((static_cast<size_t>(p->count) * 4 + kCountersAlign - 1) / kCountersAlign) * kCountersAlign;
+    return counters + static_cast<size_t>(p->ntiles) * sizeof(float2) + 16;
+}
+
+ff_status validate(const ff_batch_instance* inst, int count)
+{
+    if (count < 0 || (count > 0 && inst == nullptr)) return FF_ERR_INVALID_ARG;
+    for (int i = 0; i < count; ++i) {
+        const ff_batch_instance& b = inst[i];
+        if (b.n < 0 || (b.kind != FF_BATCH_DOT && b.kind != FF_BATCH_AXPY)) return FF_ERR_INVALID_ARG;
+        const size_t n = static_cast<size_t>(b.n);
+        if (!ffh::ok_ptr(b.x, n) || !ffh::ok_ptr(b.y, n)) return FF_ERR_INVALID_ARG;
+        if (b.kind == FF_BATCH_DOT && !ffh::ok_ptr(b.out, 1)) return FF_ERR_INVALID_ARG;
+        if (b.kind == FF_BATCH_AXPY && !ffh::ok_ptr(b.out, n)) return FF_ERR_INVALID_ARG;
+    }
+    return FF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ff_status ff_batch_plan_create(const ff_batch_instance* inst, int count, const ff_tune* tune_or_null,
+                               ff_batch_plan** out)
+{
+    if (!out) return FF_ERR_INVALID_ARG;
+    *out = nullptr;
+    ff_status st = validate(inst, count);
+    if (st != FF_OK) return st;
+    ff_tune tune = tune_or_null ? *tune_or_null : kDefaultTune;
+    const Variant* var = find_variant(tune.block, tune.pairs_per_thread);
+    if (!var || tune.blocks_per_sm < 0 || tune.blocks_per_sm > 32) return FF_ERR_INVALID_ARG;
+    ffh::DeviceInfo di;
+    st = ffh::device_info(&di);
+    if (st != FF_OK) return st;
+
+    const int64_t tile = static_cast<int64_t>(tune.block) * tune.pairs_per_thread;
+    std::vector<DevInst> hi(static_cast<size_t>(count));
+    std::vector<Tile> ht;
+    int64_t ndot = 0, total = 0;
+    for (int i = 0; i < count; ++i) {
+        const ff_batch_instance& b = inst[i];
+        DevInst& d = hi[static_cast<size_t>(i)];
+        d.x = reinterpret_cast<const float2*>(b.x);
+        d.y = reinterpret_cast<const float2*>(b.y);
+        d.out = reinterpret_cast<float2*>(b.out);
+        d.alpha = make_float2(b.alpha.hi, b.alpha.lo);
+        d.n = b.n;
+        d.kind = b.kind;
+        d.vec = (ffh::aligned(b.x, 16) && ffh::aligned(b.y, 16) &&
+                 (b.kind == FF_BATCH_DOT || ffh::aligned(b.out, 16))) ? 1 : 0;
+        d.first_tile = static_cast<int64_t>(ht.size());
+        // a dot of length 0 still needs one tile to write its (0, 0)
+        const int64_t nt = b.n > 0 ? (b.n + tile - 1) / tile : (b.kind == FF_BATCH_DOT ? 1 : 0);
+        if (nt > INT32_MAX) return FF_ERR_INVALID_ARG;
+        d.ntiles = static_cast<int32_t>(nt);
+        d.pad = 0;
+        for (int64_t k = 0; k < nt; ++k) ht.push_back(Tile{i, 0, k * tile});
+        ndot += (b.kind == FF_BATCH_DOT);
+        total += b.n;
+    }
+    auto* p = new (std::nothrow) ff_batch_plan();
+    if (!p) return FF_ERR_UNSUPPORTED;
+    p->count = count;
+    p->tune = tune;
+    p->ntiles = static_cast<int64_t>(ht.size());
+    p->ndot = ndot;
+    p->total_values = total;
+    p->device = di.device;
+    int bps = tune.blocks_per_sm;
+    if (bps == 0) bps = ffh::occupancy(reinterpret_cast<const void*>(var->fn), tune.block);
+    int64_t grid = static_cast<int64_t>(di.sm_count) * (bps > 0 ? bps : 1);
+    if (grid > p->ntiles) grid = p->ntiles > 0 ? p->ntiles : 1;
+    p->grid = static_cast<unsigned>(grid);
+    p->d_inst = nullptr;
+    p->d_tiles = nullptr;
+    if (count > 0) {
+        cudaError_t e = cudaMalloc(&p->d_inst, hi.size() * sizeof(DevInst));
+        if (e == cudaSuccess && !ht.empty()) e = cudaMalloc(&p->d_tiles, ht.size() * sizeof(Tile));
+        if (e == cudaSuccess) e = cudaMemcpy(p->d_inst, hi.data(), hi.size() * sizeof(DevInst), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && !ht.empty())
+            e = cudaMemcpy(p->d_tiles, ht.data(), ht.size() * sizeof(Tile), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(p->d_inst);
+            cudaFree(p->d_tiles);
+            delete p;
+            return ffh::cuda_status(e);
+        }
+    }
+    *out = p;
+    return FF_OK;
+}
+
+size_t ff_batch_workspace_bytes(const ff_batch_plan* p) { return p ? ws_bytes_for(p) : 0; }
+
+ff_status ff_batch_plan_info(const ff_batch_plan* p, ff_tune* tune, int64_t* ntiles, unsigned* grid)
+{
+    if (!p) return FF_ERR_INVALID_ARG;
+    if (tune) *tune = p->tune;
+    if (ntiles) *ntiles = p->ntiles;
+    if (grid) *grid = p->grid;
+    return FF_OK;
+}
+
+ff_status ff_batch_run(const ff_batch_plan* p, void* ws, size_t ws_bytes, cudaStream_t s)
+{
+    if (!p) return FF_ERR_INVALID_ARG;
+    if (p->ntiles == 0) return FF_OK;
+    if (ws == nullptr || ws_bytes < ws_bytes_for(p) || !ffh::aligned(ws, 16)) return FF_ERR_WORKSPACE;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != p->device) return FF_ERR_INVALID_ARG;
+    const Variant* var = find_variant(p->tune.block, p->tune.pairs_per_thread);
+    if (!var) return FF_ERR_INVALID_ARG;
+    auto* counters = static_cast<unsigned*>(ws);
+    const size_t cbytes = ((static_cast<size_t>(p->count) * 4 + kCountersAlign - 1) / kCountersAlign) * kCountersAlign;
+    auto* partials = reinterpret_cast<float2*>(static_cast<char*>(ws) + cbytes);
+    ff_status st = ffh::cuda_status(cudaMemsetAsync(counters, 0, static_cast<size_t>(p->count) * 4, s));
+    if (st != FF_OK) return st;
+    var->fn<<<p->grid, p->tune.block, 0, s>>>(p->d_inst, p->d_tiles, p->ntiles, partials, counters);
+    return ffh::check_launch();
+}
+
+void ff_batch_plan_destroy(ff_batch_plan* p)
+{
+    if (!p) return;
+    cudaFree(p->d_inst);
+    cudaFree(p->d_tiles);
+    delete p;
+}
+
+ff_status ff_batch_graph_create(const ff_batch_plan* p, void* ws, size_t ws_bytes, ff_batch_graph** out)
+{
+    if (!p || !out) return FF_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (p->ntiles > 0 && (ws == nullptr || ws_bytes < ws_bytes_for(p) || !ffh::aligned(ws, 16)))
+        return FF_ERR_WORKSPACE;
+    cudaStream_t cs = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return ffh::cuda_status(e);
+    auto* g = new (std::nothrow) ff_batch_graph();
+    if (!g) {
+        cudaStreamDestroy(cs);
+        return FF_ERR_UNSUPPORTED;
+    }
+    g->graph = nullptr;
+    g->exec = nullptr;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    ff_status st = FF_OK;
+    if (e == cudaSuccess) {
+        st = ff_batch_run(p, ws, ws_bytes, cs);
+        cudaError_t e2 = cudaStreamEndCapture(cs, &g->graph);
+        if (st == FF_OK && e2 != cudaSuccess) st = ffh::cuda_status(e2);
+    } else {
+        st = ffh::cuda_status(e);
+    }
+    if (st == FF_OK) st = ffh::cuda_status(cudaGraphInstantiate(&g->exec, g->graph, 0));
+    cudaStreamDestroy(cs);
+    if (st != FF_OK) {
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        if (g->graph) cudaGraphDestroy(g->graph);
+        delete g;
+        return st;
+    }
+    *out = g;
+    return FF_OK;
+}
+
+ff_status ff_batch_graph_launch(ff_batch_graph* g, cudaStream_t s)
+{
+    if (!g) return FF_ERR_INVALID_ARG;
+    return ffh::cuda_status(cudaGraphLaunch(g->exec, s));
+}
+
+void ff_batch_graph_destroy(ff_batch_graph* g)
+{
+    if (!g) return;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
+}
+
+int ff_batch_tune_candidates(ff_tune* out, int max)
+{
+    const int per = 3;  // blocks per SM: occupancy-limited (0), 2, 4
+    const int bps[per] = {0, 2, 4};
+    int k = 0;
+    for (const Variant& v : kVariants)
+        for (int b = 0; b < per; ++b) {
+            if (out && k < max) out[k] = ff_tune{v.block, v.ppt, bps[b]};
+            ++k;
+        }
+    return k;
+}
+
+size_t ff_batch_autotune_workspace_bytes(const ff_batch_instance* inst, int count)
+{
+    if (count < 0 || (count > 0 && !inst)) return 0;
+    // the smallest tile of any candidate gives the most tiles
+    int64_t smallest = INT64_MAX;
+    for (const Variant& v : kVariants) smallest = std::min<int64_t>(smallest, static_cast<int64_t>(v.block) * v.ppt);
+    size_t ntiles = 0;
+    for (int i = 0; i < count; ++i) {
+        const int64_t n = inst[i].n;
+        ntiles += static_cast<size_t>(n > 0 ? (n + smallest - 1) / smallest : 1);
+    }
+    const size_t counters = ((static_cast<size_t>(count) * 4 + kCountersAlign - 1) / kCountersAlign) * kCountersAlign;
+    return counters + ntiles * sizeof(float2) + 16;
+}
+
+ff_status ff_batch_autotune(const ff_batch_instance* inst, int count, void* ws, size_t ws_bytes, cudaStream_t s,
+                            int reps, ff_tune* best, float* best_ms)
+{
+    if (!best) return FF_ERR_INVALID_ARG;
+    ff_status st = validate(inst, count);
+    if (st != FF_OK) return st;
+    if (reps < 1) reps = 1;
+    const int nc = ff_batch_tune_candidates(nullptr, 0);
+    std::vector<ff_tune> cands(static_cast<size_t>(nc));
+    ff_batch_tune_candidates(cands.data(), nc);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    st = ffh::cuda_status(cudaEventCreate(&e0));
+    if (st == FF_OK) st = ffh::cuda_status(cudaEventCreate(&e1));
+    float best_t = -1.0f;
+    ff_tune best_tune = kDefaultTune;
+    for (int c = 0; c < nc && st == FF_OK; ++c) {
+        ff_batch_plan* p = nullptr;
+        st = ff_batch_plan_create(inst, count, &cands[static_cast<size_t>(c)], &p);
+        if (st != FF_OK) break;
+        if (ws_bytes < ws_bytes_for(p)) {
+            ff_batch_plan_destroy(p);
+            st = FF_ERR_WORKSPACE;
+            break;
+        }
+        st = ff_batch_run(p, ws, ws_bytes, s);  // warm-up
+        if (st == FF_OK) st = ffh::cuda_status(cudaEventRecord(e0, s));
+        for (int r = 0; r < reps && st == FF_OK; ++r) st = ff_batch_run(p, ws, ws_bytes, s);
+        if (st == FF_OK) st = ffh::cuda_status(cudaEventRecord(e1, s));
+        if (st == FF_OK) st = ffh::cuda_status(cudaEventSynchronize(e1));
+        float ms = 0.0f;
+        if (st == FF_OK) st = ffh::cuda_status(cudaEventElapsedTime(&ms, e0, e1));
+        ff_batch_plan_destroy(p);
+        if (st != FF_OK) break;
+        ms /= static_cast<float>(reps);
+        if (best_t < 0.0f || ms < best_t) {
+            best_t = ms;
+            best_tune = cands[static_cast<size_t>(c)];
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st != FF_OK) return st;
+    *best = best_tune;
+    if (best_ms) *best_ms = best_t;
+    return FF_OK;
+}
+
+}  // extern "C"
