@@ -1,0 +1,140 @@
+"""Batched dot / AXPY instances in one persistent launch (and its CUDA graph
+and autotuner) against the oracle and against the plain per-instance calls.
+
+AXPY instances must match the oracle bit for bit; dot instances must stay
+within n 2^-46 sum|x_i y_i| of the exact value.  Lengths cover 0, 1, odd,
+tile-sized and multi-tile instances; some instances start 8 bytes past a
+16-byte boundary (scalar path).
+"""
+import ctypes
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_cs_0603115_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda"
+
+
+def same_bits(got, want):
+    got = np.ascontiguousarray(got, np.float32)
+    want = np.ascontiguousarray(want, np.float32)
+    nan = np.isnan(got) & np.isnan(want)
+    assert ((got.view(np.uint32) == want.view(np.uint32)) | nan).all()
+
+
+def build_case(lengths, kinds, seed):
+    from paper_cs_0603115_gb300 import batch
+    specs, keep = [], []
+    for i, (n, kind) in enumerate(zip(lengths, kinds)):
+        mis = (i % 5 == 3)   # every fifth instance starts 8 bytes off a 16-byte boundary
+        if kind == batch.DOT:
+            g = inputs.ill_dot(max(n, 4), 1e8, seed + i)
+            x, y = g.x[:n], g.y[:n]
+        else:
+            e = inputs.elementwise(n, seed + i)
+            x, y = e.a, e.b
+        xd = torch.empty((n + 1, 2), dtype=torch.float32, device=DEV)[int(mis):int(mis) + n]
+        yd = torch.empty((n + 1, 2), dtype=torch.float32, device=DEV)[int(mis):int(mis) + n]
+        xd.copy_(x)
+        yd.copy_(y)
+        alpha = inputs.scalar_ff(seed + 1000 + i)
+        out = torch.full((2,) if kind == batch.DOT else (n, 2), float("nan"), dtype=torch.float32, device=DEV)
+        specs.append((kind, xd, yd, out, (float(alpha[0]), float(alpha[1]))))
+        keep.append((kind, x.numpy(), y.numpy(), alpha.numpy(), out))
+    return specs, keep
+
+
+def check(keep):
+    from paper_cs_0603115_gb300 import batch
+    for kind, x, y, alpha, out in keep:
+        got = out.cpu().numpy()
+        if kind == batch.AXPY:
+            same_bits(got, oracle.axpy(alpha, x, y))
+        else:
+            _, _, A, E = oracle.exact_dot(x, y, got)
+            assert abs(E) <= max(1, x.shape[0]) * 2.0 ** -46 * A
+
+
+LENGTHS = [0, 1, 2, 3, 7, 100, 1000, 4095, 4096, 4097, 8191, 8192, 20001, 65536, 100003, 250000, 1, 5,
+           33, 777, 3000, 12345, 54321, 99999]
+
+
+@pytest.mark.parametrize("tune", [None, (128, 16, 0), (256, 64, 2), (512, 8, 4), (512, 64, 0)])
+def test_batch_run_matches_oracle(tune):
+    from paper_cs_0603115_gb300 import batch
+    kinds = [batch.DOT if i % 2 else batch.AXPY for i in range(len(LENGTHS))]
+    specs, keep = build_case(LENGTHS, kinds, 5000)
+    plan = batch.BatchPlan(batch.make_instances(specs), tune=tune)
+    plan.run()
+    torch.cuda.synchronize()
+    check(keep)
+    # run again: counters were left at zero, partials are overwritten
+    for _, _, _, _, out in keep:
+        out.fill_(float("nan"))
+    plan.run()
+    torch.cuda.synchronize()
+    check(keep)
+    plan.close()
+
+
+def test_batch_graph_and_plain_agree():
+    import paper_cs_0603115_gb300 as ff
+    from paper_cs_0603115_gb300 import batch
+    kinds = [batch.DOT if i % 3 else batch.AXPY for i in range(len(LENGTHS))]
+    specs, keep = build_case(LENGTHS, kinds, 7000)
+    plan = batch.BatchPlan(batch.make_instances(specs)).capture()
+    plan.launch()
+    plan.launch()
+    torch.cuda.synchronize()
+    check(keep)
+    for kind, x, y, out, alpha in specs:
+        if kind == batch.AXPY:
+            same_bits(out.cpu().numpy(), ff.axpy(alpha, x, y).cpu().numpy())
+        else:
+            want = ff.dot(x, y).cpu().numpy()
+            xs, ys = x.cpu().numpy(), y.cpu().numpy()
+            _, _, A, _ = oracle.exact_dot(xs, ys)
+            got = out.cpu().numpy()
+            diff = abs((float(got[0]) - float(want[0])) + (float(got[1]) - float(want[1])))
+            assert diff <= 2 * max(1, x.shape[0]) * 2.0 ** -46 * A
+    plan.close()
+
+
+def test_autotune_and_cache(tmp_path):
+    from paper_cs_0603115_gb300 import batch
+    kinds = [batch.DOT if i % 2 else batch.AXPY for i in range(len(LENGTHS))]
+    specs, keep = build_case(LENGTHS, kinds, 9000)
+    inst = batch.make_instances(specs)
+    cache = str(tmp_path / "tune.json")
+    tune, ms = batch.autotune(inst, reps=1, cache_path=cache)
+    assert tune in batch.candidates()
+    assert ms is not None and ms > 0
+    tune2, ms2 = batch.autotune(inst, reps=1, cache_path=cache)
+    assert tune2 == tune and ms2 is None
+    plan = batch.BatchPlan(inst, tune=tune)
+    plan.run()
+    torch.cuda.synchronize()
+    check(keep)
+    plan.close()
+
+
+def test_batch_errors():
+    from paper_cs_0603115_gb300 import _lib, batch
+    x = torch.zeros((10, 2), device=DEV)
+    out = torch.zeros((10, 2), device=DEV)
+    inst = batch.make_instances([(batch.AXPY, x, x, out, (1.0, 0.0))])
+    L = _lib.load()
+    bad = batch.make_instances([(7, x, x, out, None)])
+    h = ctypes.c_void_p()
+    assert L.ff_batch_plan_create(bad, 1, None, ctypes.byref(h)) == 1
+    t = _lib.ff_tune(256, 3, 0)     # unsupported pairs_per_thread
+    assert L.ff_batch_plan_create(inst, 1, ctypes.byref(t), ctypes.byref(h)) == 1
+    plan = batch.BatchPlan(inst)
+    assert L.ff_batch_run(plan.handle, plan.ws.data_ptr(), 8, None) == 2   # workspace too small
+    plan.close()
