@@ -133,6 +133,29 @@ FF_API ff_status ff_sum(const ff2* x, size_t n, ff2* out_dev, void* ws, size_t w
 FF_API ff_status ff_dot(const ff2* x, const ff2* y, size_t n, ff2* out_dev, void* ws, size_t ws_bytes,
                  cudaStream_t s);
 
+/* ff_dot without a workspace argument, for callers that cannot allocate
+ * device memory: a plugin whose host application owns every device
+ * allocation through its own pool and budget, or a latency-critical path on
+ * which cudaMalloc and cudaFree (which can synchronise the whole device) are
+ * not allowed.  The paper has no counterpart to this entry point.
+ *
+ * Same result as ff_dot (same launch shape, same combination order), but
+ * its scratch -- the arrival ticket and up to 2048 per-block partial sums,
+ * 16,640 bytes -- is one fixed array inside the library, present on every
+ * GPU that loads the library until the process exits.  The call allocates
+ * nothing; it clears the ticket with an asynchronous memset on stream s
+ * before its kernel.
+ *   - All calls share the one array, which keeps the previous call's
+ *     contents: calls that overlap on the GPU (on different streams, or from
+ *     different host threads without ordering) race and give wrong results.
+ *     Order them on one stream.
+ *   - The first call on each device looks up the array's device address,
+ *     with that device current; make that first call before any stream
+ *     capture.
+ *   - Returns FF_ERR_WORKSPACE when the launch would need more than 2048
+ *     partial sums (more than 256 SMs); a 152-SM GB300 needs at most 1216. */
+FF_API ff_status ff_dot_noalloc(const ff2* x, const ff2* y, size_t n, ff2* out_dev, cudaStream_t s);
+
 /* Launch shape ff_sum / ff_dot use for these arguments (nothing is
  * launched): *grid blocks of 256 threads; *head = 1 when one leading element
  * is accumulated alone by thread 0 to reach a 16-byte boundary; *vector = 1

@@ -46,6 +46,7 @@ SIGNATURES = {
     "ff_sum": (ST, [P, SZ, P, P, SZ, P]),
     "ff_dot": (ST, [P, P, SZ, P, P, SZ, P]),
     "ff_dot_backward": (ST, [P, P, P, P, P, SZ, P]),
+    "ff_dot_noalloc": (ST, [P, P, SZ, P, P]),
     "ff_reduce_launch_shape": (ST, [P, P, SZ, ctypes.POINTER(ctypes.c_uint), ctypes.POINTER(ctypes.c_int),
                                     ctypes.POINTER(ctypes.c_int)]),
     "ff_gemv": (ST, [P, I64, I64, I64, P, I64, I64, P, I64, P]),

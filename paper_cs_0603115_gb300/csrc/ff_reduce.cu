@@ -17,6 +17,8 @@
 //      arrive (atomic ticket) accumulates the block values b, b + 256, ... per
 //      thread, from zero, and reduces them with steps 2-3.
 // No block ever waits for another.
+#include <mutex>
+
 #include "ff_core.cuh"
 #include "ff_host.cuh"
 
@@ -298,3 +300,67 @@ ff_status ff_f64_dot(const double* x, const double* y, size_t n, double* out_dev
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// ff_dot_noalloc: ff_dot for callers that may not allocate device memory.
+// Its scratch (the arrival ticket and the per-block partial sums) lives in
+// one fixed array in this file instead of a caller-provided workspace.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr unsigned kNoAllocMaxBlocks = 2048;
+constexpr size_t kNoAllocScratchBytes = kPartialsOffset + kNoAllocMaxBlocks * sizeof(float2);
+}  // namespace
+
+// One copy per device that loads the library, kept until the process exits.
+static __device__ __align__(256) unsigned char g_dot_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace {
+
+// Device address of the scratch array on the current device, looked up once
+// per device (host code cannot use the symbol itself as a device pointer).
+ff_status noalloc_scratch(int dev, void** out)
+{
+    constexpr int kMaxDev = 64;
+    static void* addr[kMaxDev] = {};
+    static std::mutex mu;
+    if (dev < 0 || dev >= kMaxDev) return FF_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lk(mu);
+    if (addr[dev] == nullptr) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_dot_noalloc_scratch);
+        if (e != cudaSuccess || p == nullptr) return ffh::cuda_status(e != cudaSuccess ? e : cudaErrorInvalidSymbol);
+        addr[dev] = p;
+    }
+    *out = addr[dev];
+    return FF_OK;
+}
+
+}  // namespace
+
+extern "C" ff_status ff_dot_noalloc(const ff2* x_, const ff2* y_, size_t n, ff2* out_, cudaStream_t s)
+{
+    auto* x = reinterpret_cast<const float2*>(x_);
+    auto* y = reinterpret_cast<const float2*>(y_);
+    auto* out = reinterpret_cast<float2*>(out_);
+    if (!ffh::ok_ptr(x, n) || !ffh::ok_ptr(y, n) || !ffh::ok_ptr(out, 1)) return FF_ERR_INVALID_ARG;
+    ffh::DeviceInfo di;
+    ff_status st = ffh::device_info(&di);
+    if (st != FF_OK) return st;
+    const Shape sh = shape_for<FFDot>(x, y, n, di);
+    if (sh.grid > kNoAllocMaxBlocks) return FF_ERR_WORKSPACE;  // more partial sums than the array holds
+    void* scratch = nullptr;
+    st = noalloc_scratch(di.device, &scratch);
+    if (st != FF_OK) return st;
+    unsigned* ticket = static_cast<unsigned*>(scratch);
+    auto* partials = reinterpret_cast<float2*>(static_cast<char*>(scratch) + kPartialsOffset);
+    if (sh.grid > 1) {
+        // the previous call left its contents; the ticket must start at zero
+        st = ffh::cuda_status(cudaMemsetAsync(ticket, 0, sizeof(unsigned), s));
+        if (st != FF_OK) return st;
+    }
+    if (sh.vec)
+        reduce_kernel<FFDot, kU><<<sh.grid, kRBlock, 0, s>>>(x, y, n, sh.head, out, partials, ticket);
+    else
+        reduce_scalar_kernel<FFDot><<<sh.grid, kRBlock, 0, s>>>(x, y, n, out, partials, ticket);
+    return ffh::check_launch();
+}
