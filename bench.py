@@ -131,12 +131,20 @@ def barrier(dist):
 
 
 def max_over_ranks(dist, value: float) -> float:
+    """The slowest rank's time (timing only: the data path has no collective)."""
     if dist is None:
         return value
     import torch
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_value(world_size: int, units_per_step: int, steps: int, elapsed_max: float) -> float:
+    """Weak scaling: every rank processes its own units; the job's rate is all
+    ranks' units over the slowest rank's time."""
+    return world_size * units_per_step * steps / elapsed_max
 
 
 # ---------------------------------------------------------------------------
@@ -260,7 +268,7 @@ def run_gpu(args):
     elapsed_max = max_over_ranks(dist, elapsed)
     per_op = {op: sum(a_.elapsed_time(b_) for a_, b_ in evs[op]) / 1e3 / args.steps for op in OPS}
     ffops_step = len(OPS) * n
-    value = ws * ffops_step * args.steps / elapsed_max
+    value = whole_job_value(ws, ffops_step, args.steps, elapsed_max)
 
     rows = {}
     for op in OPS:
@@ -382,6 +390,14 @@ def extra_rows(torch, ff, inputs, e, dev, peaks):
     t = time_fn(torch, lambda: ff.dot_backward(dout, x, y, dx, dy), 10)
     out["dot_backward_2^26"] = {"ms": round(t * 1e3, 4), "GB/s": round(32 * nd / t / 1e9, 1),
                                 "frac_hbm": round(32 * nd / t / 1e9 / hbm, 4), "ff_op_s": 2 * nd / t}
+    def plain_adjoint():
+        db = dout.expand(nd, 2).contiguous()
+        ff.mul(db, y, out=dx)
+        ff.mul(db, x, out=dy)
+
+    tp = time_fn(torch, plain_adjoint, 10)
+    out["dot_backward_2^26"]["plain_two_mul_ms"] = round(tp * 1e3, 4)
+    out["dot_backward_2^26"]["speedup_vs_plain"] = round(tp / t, 3)
     x64, y64 = inputs.ff_to_f64(x), inputs.ff_to_f64(y)
     t = time_fn(torch, lambda: ff.f64_dot(x64, y64), 10)
     out["f64_dot_2^26"] = {"ms": round(t * 1e3, 4), "GB/s": round(16 * nd / t / 1e9, 1)}
@@ -420,7 +436,134 @@ def extra_rows(torch, ff, inputs, e, dev, peaks):
     out["f64_gemv_32768^2"] = f64
     del A64, X64, Xall
     torch.cuda.empty_cache()
+    out.update(batched_rows(torch, ff, inputs, dev, peaks))
     return out
+
+
+def batched_rows(torch, ff, inputs, dev, peaks):
+    """4096 dot / AXPY instances, lengths log-uniform over 1e2..1e7: one
+    persistent launch (plain run and CUDA graph) against 4096 plain calls
+    (loop and CUDA graph); then the same dots' forward and adjoint batched
+    against plain ff_dot / ff_dot_backward calls."""
+    from paper_cs_0603115_gb300 import batch
+    hbm = peaks["hbm_gbs"]
+    lengths, kinds = inputs.batch_lengths(4096, inputs.seed_for(3, 0))
+    total = sum(lengths)
+    offs, o = [], 0
+    for n in lengths:
+        offs.append(o)
+        o += n + (n & 1)                       # keep every instance 16-byte aligned
+    X = torch.empty((o, 2), dtype=torch.float32, device=dev)
+    Y = torch.empty((o, 2), dtype=torch.float32, device=dev)
+    Z = torch.empty((o, 2), dtype=torch.float32, device=dev)   # AXPY outputs / dot gradients dx
+    W = torch.empty((o, 2), dtype=torch.float32, device=dev)   # dot gradients dy
+    D = torch.empty((4096, 2), dtype=torch.float32, device=dev)
+    Dplain = torch.empty_like(D)
+    dout = torch.empty((4096, 2), dtype=torch.float32, device=dev)
+    alphas = []
+    for i, (n, kind) in enumerate(zip(lengths, kinds)):
+        sl = slice(offs[i], offs[i] + n)
+        if kind == batch.DOT:
+            g = inputs.ill_dot(n, 1e8, inputs.seed_for(3, 1) + 7 * i, device=dev)
+            X[sl].copy_(g.x)
+            Y[sl].copy_(g.y)
+            del g
+        else:
+            e = inputs.elementwise(n, inputs.seed_for(3, 2) + 7 * i, device=dev, cancel_frac=0.0)
+            X[sl].copy_(e.a)
+            Y[sl].copy_(e.b)
+            del e
+        alphas.append(tuple(float(v) for v in inputs.scalar_ff(inputs.seed_for(3, 3) + i)))
+        dout[i].copy_(inputs.scalar_ff(inputs.seed_for(3, 4) + i))
+    torch.cuda.synchronize()
+    sl = [slice(offs[i], offs[i] + lengths[i]) for i in range(4096)]
+    specs = [(k, X[sl[i]], Y[sl[i]], D[i] if k == batch.DOT else Z[sl[i]], alphas[i]) for i, k in enumerate(kinds)]
+    inst = batch.make_instances(specs)
+    bytes_total = sum(16 * n if k == batch.DOT else 24 * n for n, k in zip(lengths, kinds))
+    ffops = sum(2 * n for n in lengths)
+
+    tune, tune_ms = batch.autotune(inst, reps=2, cache_path=os.path.join(ROOT, "_build", "autotune.json"),
+                                   force=True)
+    plan = batch.BatchPlan(inst, tune=tune)
+    plan_def = batch.BatchPlan(inst)
+
+    def plain():
+        for i, k in enumerate(kinds):
+            if k == batch.DOT:
+                ff.dot(X[sl[i]], Y[sl[i]], out=Dplain[i])
+            else:
+                ff.axpy(alphas[i], X[sl[i]], Y[sl[i]], out=Z[sl[i]])
+
+    t_plain = time_fn(torch, plain, 3, warm=1)
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        plain()
+    torch.cuda.current_stream().wait_stream(s)
+    with torch.cuda.graph(g):
+        plain()
+    t_plain_graph = time_fn(torch, g.replay, 3, warm=1)
+    t_run = time_fn(torch, plan.run, 5)
+    t_run_def = time_fn(torch, plan_def.run, 5)
+    plan.capture()
+    t_graph = time_fn(torch, plan.launch, 5)
+    z_plain = Z.clone()
+    plan.launch()
+    torch.cuda.synchronize()
+    axpy_equal = bool(torch.equal(Z, z_plain))
+    # dot agreement with the plain calls, in units of sum |x_i y_i|
+    rel = 0.0
+    for i, k in enumerate(kinds):
+        if k == batch.DOT:
+            xv, yv = inputs.ff_to_f64(X[sl[i]]), inputs.ff_to_f64(Y[sl[i]])
+            a = float((xv * yv).abs().sum().item())
+            d = abs((float(D[i, 0]) - float(Dplain[i, 0])) + (float(D[i, 1]) - float(Dplain[i, 1])))
+            rel = max(rel, d / a if a > 0 else d)
+    rows = {"batched_4096_dot_axpy": {
+        "values": total, "plain_loop_ms": round(t_plain * 1e3, 3), "plain_graph_ms": round(t_plain_graph * 1e3, 3),
+        "batched_run_ms": round(t_run * 1e3, 3), "batched_graph_ms": round(t_graph * 1e3, 3),
+        "batched_default_tune_ms": round(t_run_def * 1e3, 3),
+        "speedup_vs_plain_loop": round(t_plain / t_graph, 3), "speedup_vs_plain_graph": round(t_plain_graph / t_graph, 3),
+        "GB/s": round(bytes_total / t_graph / 1e9, 1), "frac_hbm": round(bytes_total / t_graph / 1e9 / hbm, 4),
+        "ff_op_s": ffops / t_graph, "tune": list(tune), "tune_ms": tune_ms, "ntiles": plan.ntiles,
+        "grid": plan.grid, "axpy_bitequal_plain": axpy_equal,
+        "dot_max_absdiff_vs_plain_over_sum_abs": rel}}
+    plan.close()
+    plan_def.close()
+    del g
+
+    # the dots alone: forward and adjoint, batched vs plain
+    dots = [i for i, k in enumerate(kinds) if k == batch.DOT]
+    fwd = batch.make_instances([(batch.DOT, X[sl[i]], Y[sl[i]], D[i], None) for i in dots])
+    bwd = batch.make_instances([(batch.DOT_GRAD, X[sl[i]], Y[sl[i]], Z[sl[i]], None, W[sl[i]], dout[i])
+                                for i in dots])
+    nd = sum(lengths[i] for i in dots)
+    pf = batch.BatchPlan(fwd, tune=batch.autotune(fwd, reps=2, cache_path=None)[0]).capture()
+    pb = batch.BatchPlan(bwd, tune=batch.autotune(bwd, reps=2, cache_path=None)[0]).capture()
+
+    def plain_f():
+        for j, i in enumerate(dots):
+            ff.dot(X[sl[i]], Y[sl[i]], out=Dplain[i])
+
+    def plain_b():
+        for j, i in enumerate(dots):
+            ff.dot_backward(dout[i], X[sl[i]], Y[sl[i]], Z[sl[i]], W[sl[i]])
+
+    tf_plain = time_fn(torch, plain_f, 3, warm=1)
+    tb_plain = time_fn(torch, plain_b, 3, warm=1)
+    tf = time_fn(torch, pf.launch, 5)
+    tb = time_fn(torch, pb.launch, 5)
+    rows["batched_2048_dot_fwd_grad"] = {
+        "values": nd, "fwd_plain_ms": round(tf_plain * 1e3, 3), "fwd_batched_graph_ms": round(tf * 1e3, 3),
+        "bwd_plain_ms": round(tb_plain * 1e3, 3), "bwd_batched_graph_ms": round(tb * 1e3, 3),
+        "fwd_speedup": round(tf_plain / tf, 3), "bwd_speedup": round(tb_plain / tb, 3),
+        "fwd_frac_hbm": round(16 * nd / tf / 1e9 / hbm, 4), "bwd_frac_hbm": round(32 * nd / tb / 1e9 / hbm, 4)}
+    pf.close()
+    pb.close()
+    del X, Y, Z, W, D, Dplain, dout
+    torch.cuda.empty_cache()
+    return rows
 
 
 # ---------------------------------------------------------------------------

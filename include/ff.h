@@ -197,13 +197,19 @@ FF_API ff_status ff_gemv_t(const ff2* A, int64_t m, int64_t n, int64_t lda, cons
 /* Batched dot / AXPY: many instances in one persistent launch               */
 /* ------------------------------------------------------------------------ */
 
-typedef enum ff_batch_kind { FF_BATCH_DOT = 0, FF_BATCH_AXPY = 1 } ff_batch_kind;
+typedef enum ff_batch_kind { FF_BATCH_DOT = 0, FF_BATCH_AXPY = 1, FF_BATCH_DOT_GRAD = 2 } ff_batch_kind;
 
-/* One instance.  DOT: *out = sum_i Mul22(x[i], y[i]) (out: one ff2 on the
- * device), with the Add22 accumulation of ff_dot.  AXPY: out[i] =
- * Add22(Mul22(alpha, x[i]), y[i]) for i < n (out: n values), bit-identical to
- * ff_axpy.  All pointers are device pointers owned by the caller and must
- * stay valid while any plan or graph built from the instance is used. */
+/* One instance.
+ *   DOT:      *out = sum_i Mul22(x[i], y[i]) (out: one ff2), with the Add22
+ *             accumulation of ff_dot.
+ *   AXPY:     out[i] = Add22(Mul22(alpha, x[i]), y[i]) for i < n (out: n
+ *             values), bit-identical to ff_axpy.
+ *   DOT_GRAD: the adjoint of a dot: out[i] = Mul22(*dout, y[i]) and
+ *             out2[i] = Mul22(*dout, x[i]) (dout: one ff2 read on the device
+ *             when the run executes), bit-identical to ff_dot_backward.
+ * All pointers are device pointers owned by the caller and must stay valid
+ * while any plan or graph built from the instance is used; unused pointers
+ * may be NULL. */
 typedef struct ff_batch_instance {
     int32_t kind;
     int32_t reserved;
@@ -211,6 +217,8 @@ typedef struct ff_batch_instance {
     const ff2* x;
     const ff2* y;
     ff2* out;
+    ff2* out2;
+    const ff2* dout;
     ff2 alpha;
 } ff_batch_instance;
 

@@ -21,22 +21,29 @@ from ._lib import ff2, ff_batch_instance, ff_tune
 
 DOT = 0
 AXPY = 1
+DOT_GRAD = 2
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "ff_gb300", "autotune.json")
 
 
 def make_instances(specs) -> ctypes.Array:
-    """specs: iterable of (kind, x, y, out, alpha) with x, y, out CUDA
-    float-float tensors (out is a (2,) tensor for DOT) and alpha a (hi, lo)
-    pair (ignored for DOT)."""
+    """specs: iterable of (kind, x, y, out, alpha) or (kind, x, y, out, alpha,
+    out2, dout) with x, y, out CUDA float-float tensors (out is a (2,) tensor
+    for DOT), alpha a (hi, lo) pair (AXPY only), and for DOT_GRAD out = dx,
+    out2 = dy and dout a (2,) device tensor."""
     specs = list(specs)
     arr = (ff_batch_instance * len(specs))()
-    for i, (kind, x, y, out, alpha) in enumerate(specs):
+    for i, spec in enumerate(specs):
+        kind, x, y, out, alpha = spec[:5]
+        out2 = spec[5] if len(spec) > 5 else None
+        dout = spec[6] if len(spec) > 6 else None
         arr[i].kind = kind
         arr[i].reserved = 0
         arr[i].n = x.numel() // 2
         arr[i].x = x.data_ptr()
         arr[i].y = y.data_ptr()
         arr[i].out = out.data_ptr()
+        arr[i].out2 = out2.data_ptr() if out2 is not None else None
+        arr[i].dout = dout.data_ptr() if dout is not None else None
         a = alpha if alpha is not None else (0.0, 0.0)
         arr[i].alpha = ff2(float(a[0]), float(a[1]))
     return arr

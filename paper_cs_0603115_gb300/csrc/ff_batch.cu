@@ -11,6 +11,7 @@
 // Run: a persistent grid of (SMs x blocks per SM) blocks walks the tile list
 // round robin (block b takes tiles b, b + G, b + 2G, ...).
 //   AXPY tile: z_i = Add22(Mul22(alpha, x_i), y_i) for the tile's values.
+//   dot-gradient tile: dx_i = Mul22(dout, y_i), dy_i = Mul22(dout, x_i).
 //   dot tile:  each thread accumulates its values left to right with
 //              Add22(acc, Mul22(x_i, y_i)); the block combines threads with
 //              the shuffle-down Add22 tree of ff_dot and stores the tile's
@@ -31,6 +32,8 @@ struct DevInst {
     const float2* x;
     const float2* y;
     float2* out;
+    float2* out2;
+    const float2* dout;
     float2 alpha;
     int64_t n;
     int64_t first_tile;
@@ -167,6 +170,54 @@ batch_kernel(const DevInst* __restrict__ insts, const Tile* __restrict__ tiles, 
                 }
                 __syncthreads();
             }
+        } else if (I.kind == FF_BATCH_DOT_GRAD) {
+            const float2 d = __ldg(I.dout);
+            if (I.vec) {
+                const float4* xv = reinterpret_cast<const float4*>(I.x + s0);
+                const float4* yv = reinterpret_cast<const float4*>(I.y + s0);
+                float4* dxv = reinterpret_cast<float4*>(I.out + s0);
+                float4* dyv = reinterpret_cast<float4*>(I.out2 + s0);
+                const int64_t len = s1 - s0;
+                const int64_t nch = len >> 1;
+#pragma unroll 1
+                for (int j0 = 0; j0 < CH; j0 += U) {
+                    float4 xs[U], ys[U];
+                    bool ok[U];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const int64_t c = threadIdx.x + static_cast<int64_t>(j0 + u) * BLOCK;
+                        ok[u] = c < nch;
+                        if (ok[u]) {
+                            xs[u] = __ldcs(xv + c);
+                            ys[u] = __ldcs(yv + c);
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        if (ok[u]) {
+                            const int64_t c = threadIdx.x + static_cast<int64_t>(j0 + u) * BLOCK;
+                            const float2 gx0 = ffk::mul22(d, make_float2(ys[u].x, ys[u].y));
+                            const float2 gx1 = ffk::mul22(d, make_float2(ys[u].z, ys[u].w));
+                            const float2 gy0 = ffk::mul22(d, make_float2(xs[u].x, xs[u].y));
+                            const float2 gy1 = ffk::mul22(d, make_float2(xs[u].z, xs[u].w));
+                            __stcs(dxv + c, make_float4(gx0.x, gx0.y, gx1.x, gx1.y));
+                            __stcs(dyv + c, make_float4(gy0.x, gy0.y, gy1.x, gy1.y));
+                        }
+                    }
+                }
+                if ((len & 1) && threadIdx.x == 0) {
+                    I.out[s1 - 1] = ffk::mul22(d, I.y[s1 - 1]);
+                    I.out2[s1 - 1] = ffk::mul22(d, I.x[s1 - 1]);
+                }
+            } else {
+                for (int j = 0; j < PPT; ++j) {
+                    const int64_t i = s0 + threadIdx.x + static_cast<int64_t>(j) * BLOCK;
+                    if (i < s1) {
+                        I.out[i] = ffk::mul22(d, I.y[i]);
+                        I.out2[i] = ffk::mul22(d, I.x[i]);
+                    }
+                }
+            }
         } else {
             const float2 al = I.alpha;
             if (I.vec) {
@@ -248,11 +299,15 @@ ff_status validate(const ff_batch_instance* inst, int count)
     if (count < 0 || (count > 0 && inst == nullptr)) return FF_ERR_INVALID_ARG;
     for (int i = 0; i < count; ++i) {
         const ff_batch_instance& b = inst[i];
-        if (b.n < 0 || (b.kind != FF_BATCH_DOT && b.kind != FF_BATCH_AXPY)) return FF_ERR_INVALID_ARG;
+        if (b.n < 0 || (b.kind != FF_BATCH_DOT && b.kind != FF_BATCH_AXPY && b.kind != FF_BATCH_DOT_GRAD))
+            return FF_ERR_INVALID_ARG;
         const size_t n = static_cast<size_t>(b.n);
         if (!ffh::ok_ptr(b.x, n) || !ffh::ok_ptr(b.y, n)) return FF_ERR_INVALID_ARG;
         if (b.kind == FF_BATCH_DOT && !ffh::ok_ptr(b.out, 1)) return FF_ERR_INVALID_ARG;
         if (b.kind == FF_BATCH_AXPY && !ffh::ok_ptr(b.out, n)) return FF_ERR_INVALID_ARG;
+        if (b.kind == FF_BATCH_DOT_GRAD &&
+            (!ffh::ok_ptr(b.out, n) || !ffh::ok_ptr(b.out2, n) || (n > 0 && !ffh::ok_ptr(b.dout, 1))))
+            return FF_ERR_INVALID_ARG;
     }
     return FF_OK;
 }
@@ -285,11 +340,14 @@ ff_status ff_batch_plan_create(const ff_batch_instance* inst, int count, const f
         d.x = reinterpret_cast<const float2*>(b.x);
         d.y = reinterpret_cast<const float2*>(b.y);
         d.out = reinterpret_cast<float2*>(b.out);
+        d.out2 = reinterpret_cast<float2*>(b.out2);
+        d.dout = reinterpret_cast<const float2*>(b.dout);
         d.alpha = make_float2(b.alpha.hi, b.alpha.lo);
         d.n = b.n;
         d.kind = b.kind;
         d.vec = (ffh::aligned(b.x, 16) && ffh::aligned(b.y, 16) &&
-                 (b.kind == FF_BATCH_DOT || ffh::aligned(b.out, 16))) ? 1 : 0;
+                 (b.kind == FF_BATCH_DOT || ffh::aligned(b.out, 16)) &&
+                 (b.kind != FF_BATCH_DOT_GRAD || ffh::aligned(b.out2, 16))) ? 1 : 0;
         d.first_tile = static_cast<int64_t>(ht.size());
         // a dot of length 0 still needs one tile to write its (0, 0)
         const int64_t nt = b.n > 0 ? (b.n + tile - 1) / tile : (b.kind == FF_BATCH_DOT ? 1 : 0);

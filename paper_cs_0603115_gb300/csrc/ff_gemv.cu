@@ -219,32 +219,31 @@ int64_t row_blocks(int64_t m, int64_t n, int sm_count)
 // ---------------------------------------------------------------------------
 // binary64 GEMV (one warp per row, fma accumulation, shuffle tree)
 // ---------------------------------------------------------------------------
+template <int KT>
 __global__ void __launch_bounds__(kGBlock)
 gemv_f64_kernel(const double* __restrict__ A, int64_t m, int64_t n, int64_t lda, const double* __restrict__ X,
-                int64_t ldx, int64_t k0, int kt, double* __restrict__ Y, int64_t ldy)
+                int64_t ldx, double* __restrict__ Y, int64_t ldy)
 {
     const int lane = threadIdx.x & 31;
     const int64_t r = static_cast<int64_t>(blockIdx.x) * kGWarps + (threadIdx.x >> 5);
     if (r >= m) return;
-    double acc[16];
+    double acc[KT];
 #pragma unroll
-    for (int c = 0; c < 16; ++c) acc[c] = 0.0;
+    for (int c = 0; c < KT; ++c) acc[c] = 0.0;
     const double* Ar = A + r * lda;
     for (int64_t j = lane; j < n; j += 32) {
         const double a = __ldcs(Ar + j);
 #pragma unroll
-        for (int c = 0; c < 16; ++c)
-            if (c < kt) acc[c] = __fma_rn(a, __ldg(X + (k0 + c) * ldx + j), acc[c]);
+        for (int c = 0; c < KT; ++c) acc[c] = __fma_rn(a, __ldg(X + c * ldx + j), acc[c]);
     }
 #pragma unroll
-    for (int c = 0; c < 16; ++c) {
+    for (int c = 0; c < KT; ++c) {
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) acc[c] = __dadd_rn(acc[c], __shfl_down_sync(0xffffffffu, acc[c], off));
     }
     if (lane == 0) {
 #pragma unroll
-        for (int c = 0; c < 16; ++c)
-            if (c < kt) Y[(k0 + c) * ldy + r] = acc[c];
+        for (int c = 0; c < KT; ++c) Y[c * ldy + r] = acc[c];
     }
 }
 
@@ -360,11 +359,20 @@ ff_status ff_f64_gemv(const double* A, int64_t m, int64_t n, int64_t lda, const 
         return FF_ERR_INVALID_ARG;
     if (m == 0) return FF_OK;
     const unsigned grid = static_cast<unsigned>((m + kGWarps - 1) / kGWarps);
-    for (int64_t c0 = 0; c0 < k; c0 += 16) {
-        const int kt = static_cast<int>(k - c0 < 16 ? k - c0 : 16);
-        gemv_f64_kernel<<<grid, kGBlock, 0, s>>>(A, m, n, lda, X, ldx, c0, kt, Y, ldy);
+    for (int64_t c0 = 0; c0 < k;) {
+        const int kt = tile_for(k - c0);
+        const double* Xc = X + c0 * ldx;
+        double* Yc = Y + c0 * ldy;
+        switch (kt) {
+        case 16: gemv_f64_kernel<16><<<grid, kGBlock, 0, s>>>(A, m, n, lda, Xc, ldx, Yc, ldy); break;
+        case 8: gemv_f64_kernel<8><<<grid, kGBlock, 0, s>>>(A, m, n, lda, Xc, ldx, Yc, ldy); break;
+        case 4: gemv_f64_kernel<4><<<grid, kGBlock, 0, s>>>(A, m, n, lda, Xc, ldx, Yc, ldy); break;
+        case 2: gemv_f64_kernel<2><<<grid, kGBlock, 0, s>>>(A, m, n, lda, Xc, ldx, Yc, ldy); break;
+        default: gemv_f64_kernel<1><<<grid, kGBlock, 0, s>>>(A, m, n, lda, Xc, ldx, Yc, ldy); break;
+        }
         ff_status st = ffh::check_launch();
         if (st != FF_OK) return st;
+        c0 += kt;
     }
     return FF_OK;
 }

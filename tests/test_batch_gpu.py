@@ -45,6 +45,12 @@ def build_case(lengths, kinds, seed):
         yd.copy_(y)
         alpha = inputs.scalar_ff(seed + 1000 + i)
         out = torch.full((2,) if kind == batch.DOT else (n, 2), float("nan"), dtype=torch.float32, device=DEV)
+        if kind == batch.DOT_GRAD:
+            out2 = torch.full((n + 1, 2), float("nan"), dtype=torch.float32, device=DEV)[int(mis):int(mis) + n]
+            dout = alpha.to(DEV)
+            specs.append((kind, xd, yd, out, None, out2, dout))
+            keep.append((kind, x.numpy(), y.numpy(), alpha.numpy(), (out, out2)))
+            continue
         specs.append((kind, xd, yd, out, (float(alpha[0]), float(alpha[1]))))
         keep.append((kind, x.numpy(), y.numpy(), alpha.numpy(), out))
     return specs, keep
@@ -53,6 +59,11 @@ def build_case(lengths, kinds, seed):
 def check(keep):
     from paper_cs_0603115_gb300 import batch
     for kind, x, y, alpha, out in keep:
+        if kind == batch.DOT_GRAD:
+            dx, dy = oracle.dot_backward(alpha, x, y)
+            same_bits(out[0].cpu().numpy(), dx)
+            same_bits(out[1].cpu().numpy(), dy)
+            continue
         got = out.cpu().numpy()
         if kind == batch.AXPY:
             same_bits(got, oracle.axpy(alpha, x, y))
@@ -76,8 +87,21 @@ def test_batch_run_matches_oracle(tune):
     check(keep)
     # run again: counters were left at zero, partials are overwritten
     for _, _, _, _, out in keep:
-        out.fill_(float("nan"))
+        for t in (out if isinstance(out, tuple) else (out,)):
+            t.fill_(float("nan"))
     plan.run()
+    torch.cuda.synchronize()
+    check(keep)
+    plan.close()
+
+
+@pytest.mark.parametrize("tune", [None, (256, 16, 0)])
+def test_batch_with_dot_gradients(tune):
+    from paper_cs_0603115_gb300 import batch
+    kinds = [(batch.DOT, batch.AXPY, batch.DOT_GRAD)[i % 3] for i in range(len(LENGTHS))]
+    specs, keep = build_case(LENGTHS, kinds, 6000)
+    plan = batch.BatchPlan(batch.make_instances(specs), tune=tune).capture()
+    plan.launch()
     torch.cuda.synchronize()
     check(keep)
     plan.close()
