@@ -285,26 +285,50 @@ def run_gpu(args):
                 "algorithmic_bytes_per_launch": BYTES_PER_VALUE[dom] * n,
                 "peak_source": peaks["source"] + " copy bandwidth"}
 
-    # end to end through host buffers: H2D of the step's inputs, the six C-ABI
-    # calls, D2H of every result, per step
+    # end to end through host buffers: every step copies its inputs from
+    # pinned host memory, runs the six C-ABI calls and copies every result
+    # back.  The step is cut into chunks pipelined over three streams
+    # (host-to-device copies, kernels, device-to-host copies) so that both
+    # directions of the host link and the GPU work at once.
     e2e = None
     if not args.no_e2e:
-        host_in = {k: torch.empty_like(getattr(e, k), device="cpu").pin_memory() for k in ("a", "b", "ab", "a_sqrt")}
+        keys = ("a", "b", "ab", "a_sqrt")
+        host_in = {k: torch.empty_like(getattr(e, k), device="cpu").pin_memory() for k in keys}
         for k, t in host_in.items():
             t.copy_(getattr(e, k))
         host_out = torch.empty_like(e.a, device="cpu").pin_memory()
-        dev_in = {k: torch.empty_like(getattr(e, k)) for k in host_in}
-        from types import SimpleNamespace
-        de = SimpleNamespace(**dev_in)
-        st2 = make_step(ff, de, outs)
+        dev_in = {k: torch.empty_like(getattr(e, k)) for k in keys}
+        s_h2d, s_cmp, s_d2h = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+        chunks = 16
+        csz = (n + chunks - 1) // chunks
         e2e_steps = max(1, min(args.steps, 5))
+        from types import SimpleNamespace
 
         def one_e2e():
-            for k, t in host_in.items():
-                dev_in[k].copy_(t, non_blocking=True)
-            for op in OPS:
-                st2[op]()
-                host_out.copy_(outs[OPS.index(op)], non_blocking=True)
+            # a step may overwrite the device inputs once the previous step's
+            # kernels finished, and the outputs once they were copied out
+            s_h2d.wait_stream(s_cmp)
+            s_cmp.wait_stream(s_d2h)
+            for c in range(chunks):
+                lo, hi = c * csz, min(n, (c + 1) * csz)
+                ev_in, ev_out = torch.cuda.Event(), torch.cuda.Event()
+                with torch.cuda.stream(s_h2d):
+                    for k in keys:
+                        dev_in[k][lo:hi].copy_(host_in[k][lo:hi], non_blocking=True)
+                    ev_in.record(s_h2d)
+                with torch.cuda.stream(s_cmp):
+                    s_cmp.wait_event(ev_in)
+                    de = SimpleNamespace(**{k: dev_in[k][lo:hi] for k in keys})
+                    step_c = make_step(ff, de, [o[lo:hi] for o in outs])
+                    for op in OPS:
+                        step_c[op]()
+                    ev_out.record(s_cmp)
+                with torch.cuda.stream(s_d2h):
+                    s_d2h.wait_event(ev_out)
+                    for o in outs:
+                        host_out[lo:hi].copy_(o[lo:hi], non_blocking=True)
+            for st_ in (s_h2d, s_cmp, s_d2h):
+                torch.cuda.current_stream().wait_stream(st_)
 
         one_e2e()
         torch.cuda.synchronize()
@@ -317,8 +341,9 @@ def run_gpu(args):
         h2d = sum(t.numel() * t.element_size() for t in host_in.values())
         d2h = len(OPS) * host_out.numel() * host_out.element_size()
         e2e = {"value": ws * ffops_step * e2e_steps / e_el, "unit": UNIT, "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "steps": e2e_steps, "host_buffers": "pinned"}
-        del host_in, host_out, dev_in, de, st2
+               "d2h_bytes_per_step": d2h, "steps": e2e_steps, "host_buffers": "pinned",
+               "pipeline": f"{chunks} chunks over 3 streams", "link_GB/s": round((h2d + d2h) * e2e_steps / e_el / 1e9, 1)}
+        del host_in, host_out, dev_in
         torch.cuda.synchronize()
 
     cpu = None
@@ -372,6 +397,23 @@ def extra_rows(torch, ff, inputs, e, dev, peaks):
         t = time_fn(torch, fn, 5)
         out[name] = {"ms": round(t * 1e3, 4), "GB/s": round(nb * n / t / 1e9, 1), "op_s": n / t}
     del a32, b32, c32, o32
+    # accurate float-float addition on the same operands (24 B per value)
+    oacc = torch.empty_like(e.a)
+    t = time_fn(torch, lambda: ff.add_accurate(e.a, e.b, out=oacc), 5)
+    out["add_accurate"] = {"ms": round(t * 1e3, 4), "GB/s": round(24 * n / t / 1e9, 1),
+                           "frac_hbm": round(24 * n / t / 1e9 / hbm, 4), "ff_op_s": n / t}
+    del oacc
+    torch.cuda.empty_cache()
+    # compensated Sum2 / Dot2 of binary32 vectors, n = 2^26 (4 / 8 B per value)
+    nd2 = 1 << 26
+    g2 = inputs.ill_dot_f32(nd2, 1e12, inputs.seed_for(5, 12), device=dev)
+    t = time_fn(torch, lambda: ff.dot2(g2.x, g2.y), 10)
+    out["dot2_f32_2^26"] = {"ms": round(t * 1e3, 4), "GB/s": round(8 * nd2 / t / 1e9, 1),
+                            "frac_hbm": round(8 * nd2 / t / 1e9 / hbm, 4), "values_s": nd2 / t}
+    t = time_fn(torch, lambda: ff.sum2(g2.x), 10)
+    out["sum2_f32_2^26"] = {"ms": round(t * 1e3, 4), "GB/s": round(4 * nd2 / t / 1e9, 1),
+                            "frac_hbm": round(4 * nd2 / t / 1e9 / hbm, 4), "values_s": nd2 / t}
+    del g2
     torch.cuda.empty_cache()
 
     # reductions and the dot adjoint on the ill-conditioned dot, n = 2^26
@@ -635,6 +677,64 @@ def run_case(args):
     print(f"case {args.case} n={n} reps={args.reps} ok")
 
 
+def paper_table(args):
+    """The paper's timing method (Section 6, Tables 3 and 4) regenerated:
+    times of FP32 add / mul / mad, Add12, Mul12, Add22 and Mul22 over 4096 ..
+    1048576 values, normalised to the time of 4096 FP32 additions on the same
+    device -- on the GB300 (CUDA events, mean of 50 launches after warm-up)
+    and on one host core (the oracle's loops, the CPU-baseline leg)."""
+    import torch
+    import paper_cs_0603115_gb300 as ff
+    from paper_cs_0603115_gb300 import build as ffbuild
+    from paper_cs_0603115_gb300 import inputs
+    ffbuild.build()
+    dev = torch.device("cuda", 0)
+    sizes = [4096, 16384, 65536, 262144, 1048576]
+    cols = ["Add", "Mul", "Mad", "Add12", "Mul12", "Add22", "Mul22"]
+    gpu_t, cpu_t = {}, {}
+    for n in sizes:
+        e = inputs.elementwise(n, inputs.seed_for(0, 0), device=dev)
+        a32, b32, c32 = e.a[:, 0].contiguous(), e.b[:, 0].contiguous(), e.ab[:, 1].contiguous()
+        o32 = torch.empty_like(a32)
+        o = torch.empty_like(e.a)
+        fns = [lambda: ff.f32_add(a32, b32, out=o32), lambda: ff.f32_mul(a32, b32, out=o32),
+               lambda: ff.f32_mad(a32, b32, c32, out=o32), lambda: ff.add12(e.ab, out=o),
+               lambda: ff.mul12(e.ab, out=o), lambda: ff.add(e.a, e.b, out=o), lambda: ff.mul(e.a, e.b, out=o)]
+        gpu_t[n] = [time_fn(torch, f, 50, warm=5) for f in fns]
+        cpu_t[n] = cpu_paper_row(e)
+    base_g, base_c = gpu_t[4096][0], cpu_t[4096][0]
+    lines = ["| size | " + " | ".join(cols) + " |", "|---" * (len(cols) + 1) + "|"]
+    out = {"gpu": {}, "cpu": {}, "gpu_us_per_4096_adds": base_g * 1e6, "cpu_us_per_4096_adds": base_c * 1e6}
+    for which, tab, base in (("gpu", gpu_t, base_g), ("cpu", cpu_t, base_c)):
+        lines.append(f"| **{which}** |" + " |" * len(cols))
+        for n in sizes:
+            norm = [t / base for t in tab[n]]
+            out[which][str(n)] = [round(v, 2) for v in norm]
+            lines.append(f"| {n} | " + " | ".join(f"{v:.2f}" for v in norm) + " |")
+    print("\n".join(lines))
+    print(json.dumps(out))
+
+
+def cpu_paper_row(e):
+    """One host core running the oracle's loops for the paper-table sizes
+    (minimum of 20 runs each)."""
+    import oracle
+    a, b, ab = e.a.cpu().numpy(), e.b.cpu().numpy(), e.ab.cpu().numpy()
+    a32, b32, c32 = a[:, 0].copy(), b[:, 0].copy(), ab[:, 1].copy()
+    fns = [lambda: oracle.fp32_add(a32, b32), lambda: oracle.fp32_mul(a32, b32),
+           lambda: oracle.fp32_mad(a32, b32, c32), lambda: oracle.add12(ab), lambda: oracle.mul12(ab),
+           lambda: oracle.add22(a, b), lambda: oracle.mul22(a, b)]
+    res = []
+    for f in fns:
+        best = float("inf")
+        for _ in range(20):
+            t0 = time.perf_counter()
+            f()
+            best = min(best, time.perf_counter() - t0)
+        res.append(best)
+    return res
+
+
 def main():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -644,6 +744,7 @@ def main():
     p.add_argument("--rows", choices=["all", "main"], default="all")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--paper-table", action="store_true", help="regenerate the paper's normalised timing tables")
     p.add_argument("--case", default=None, help="profiling case: one operator on --n values, --reps launches")
     p.add_argument("--n", type=int, default=1 << 24)
     p.add_argument("--k", type=int, default=1)
@@ -651,6 +752,9 @@ def main():
     args = p.parse_args()
     if args.case:
         run_case(args)
+        return
+    if args.paper_table:
+        paper_table(args)
         return
     if args.warmup < 3:
         args.warmup = 3

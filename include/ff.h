@@ -93,6 +93,13 @@ FF_API ff_status ff_mul12(const ff2* ab, ff2* pe, size_t n, cudaStream_t s);
  * |err| <= max(2^-24 |al + bl|, 2^-44 |a + b|). */
 FF_API ff_status ff_add(const ff2* a, const ff2* b, ff2* out, size_t n, cudaStream_t s);
 
+/* Accurate float-float addition (the paper leaves Add22's cancellation error
+ * as open work, Sections 6.1 and 7): Joldes, Muller and Popescu (2017),
+ * Algorithm 6 -- TwoSum of the high parts, TwoSum of the low parts, two
+ * Fast2Sum renormalisations.  out[i] = a[i] + b[i] with relative error
+ * <= 3 2^-48 / (1 - 2^-22), also under cancellation. */
+FF_API ff_status ff_add_accurate(const ff2* a, const ff2* b, ff2* out, size_t n, cudaStream_t s);
+
 /* Mul22 theorem: out[i] = Mul22(a[i], b[i]), relative error <= 2^-44. */
 FF_API ff_status ff_mul(const ff2* a, const ff2* b, ff2* out, size_t n, cudaStream_t s);
 
@@ -172,6 +179,23 @@ FF_API ff_status ff_reduce_launch_shape(const ff2* x, const ff2* y, size_t n, un
 FF_API ff_status ff_dot_backward(const ff2* dout_dev, const ff2* x, const ff2* y, ff2* dx, ff2* dy,
                           size_t n, cudaStream_t s);
 
+/* Compensated sum and dot product of plain binary32 vectors (the paper's
+ * "compensated algorithms", Section 7): Ogita, Rump and Oishi's Sum2 and
+ * Dot2 (2005) with Add12 as TwoSum and the fused Mul12 as TwoProduct, per
+ * thread in the sweep order of ff_sum, combined across threads, warps and
+ * blocks by (p, q) = TwoSum(a.p, b.p), s = a.s + (b.s + q).  *out_dev is the
+ * float-float Add12(p, s).  x, y: 4-byte aligned binary32 arrays; ws as for
+ * ff_sum.  Reads 4 (Sum2) or 8 (Dot2) bytes per value, half of ff_sum /
+ * ff_dot, for about twice the binary32 precision. */
+FF_API ff_status ff_sum2(const float* x, size_t n, ff2* out_dev, void* ws, size_t ws_bytes, cudaStream_t s);
+FF_API ff_status ff_dot2(const float* x, const float* y, size_t n, ff2* out_dev, void* ws, size_t ws_bytes,
+                         cudaStream_t s);
+
+/* Launch shape of ff_sum2 / ff_dot2 (as ff_reduce_launch_shape; *head is up
+ * to 3 leading values, the vector sweep moves four values per step). */
+FF_API ff_status ff_reduce2_launch_shape(const float* x, const float* y, size_t n, unsigned* grid, int* head,
+                                         int* vector);
+
 /* ------------------------------------------------------------------------ */
 /* Float-float GEMV and its adjoint                                          */
 /* ------------------------------------------------------------------------ */
@@ -192,6 +216,14 @@ FF_API size_t ff_gemv_t_workspace_bytes(int64_t m, int64_t n, int64_t k);
 FF_API ff_status ff_gemv_t(const ff2* A, int64_t m, int64_t n, int64_t lda, const ff2* dY,
                     int64_t lddy, int64_t k, ff2* dX, int64_t lddx, void* ws, size_t ws_bytes,
                     cudaStream_t s);
+
+/* Weight gradient of Y = A X: dA = dY X^T, dA[r, j] = sum over c of
+ * Mul22(dY[r, c], X[j, c]), accumulated with Add22 in order c = 0 .. k-1
+ * (bit-reproducible).  dY: m x k column-major (lddy >= m); X: n x k
+ * column-major (ldx >= n); dA: m x n row-major (ldda >= n), overwritten.
+ * 1 <= k <= 64, m < 2^31. */
+FF_API ff_status ff_gemv_dA(const ff2* dY, int64_t m, int64_t lddy, const ff2* X, int64_t n, int64_t ldx,
+                            int64_t k, ff2* dA, int64_t ldda, cudaStream_t s);
 
 /* ------------------------------------------------------------------------ */
 /* Batched dot / AXPY: many instances in one persistent launch               */

@@ -52,11 +52,14 @@ def lib() -> ctypes.CDLL:
             "orc_mul12_dekker": [P, P, S], "orc_mul12": [P, P, S],
             "orc_add22": [P, P, P, S], "orc_mul22": [P, P, P, S],
             "orc_mul22_dekker": [P, P, P, S], "orc_div22": [P, P, P, S],
+            "orc_add22_accurate": [P, P, P, S], "orc_sum2": [P, S, P], "orc_dot2": [P, P, S, P],
+            "exact_dot_f32": [P, P, S, P, P],
             "orc_sqrt22": [P, P, S], "orc_sum": [P, S, P],
             "orc_dot": [P, P, S, P], "orc_dot_backward": [P, P, P, P, P, S],
             "orc_axpy": [P, P, P, P, S],
             "orc_gemv": [P, I64, I64, I64, P, I64, I64, P, I64],
             "orc_gemv_t": [P, I64, I64, I64, P, I64, I64, P, I64],
+            "orc_gemv_dA": [P, I64, I64, P, I64, I64, I64, P, I64],
             "orc_fp32_add": [P, P, P, S], "orc_fp32_mul": [P, P, P, S],
             "orc_fp32_mad": [P, P, P, P, S],
             "exact_sum_f64_q": [P, S, P], "exact_count_sum2_mismatch": [P, P, S],
@@ -129,6 +132,34 @@ def add22(a, b): return _binary("orc_add22", a, b)
 def mul22(a, b): return _binary("orc_mul22", a, b)
 def mul22_dekker(a, b): return _binary("orc_mul22_dekker", a, b)
 def div22(a, b): return _binary("orc_div22", a, b)
+def add22_accurate(a, b): return _binary("orc_add22_accurate", a, b)
+
+
+def sum2(x):
+    """Ogita-Rump-Oishi Sum2 of a binary32 vector, as an unrounded (p, s) pair."""
+    x = _f32(x).reshape(-1); out = np.empty(2, np.float32)
+    lib().orc_sum2(_p(x), x.size, _p(out)); return out
+
+
+def dot2(x, y):
+    """Ogita-Rump-Oishi Dot2 of binary32 vectors, as an unrounded (p, s) pair."""
+    x = _f32(x).reshape(-1); y = _f32(y).reshape(-1); out = np.empty(2, np.float32)
+    lib().orc_dot2(_p(x), _p(y), x.size, _p(out)); return out
+
+
+def exact_dot_f32(x, y=None, res=None):
+    """Exact reference of a binary32 dot (or sum): (S_hi, S_lo, A, E) as for
+    exact_dot, with E measured for the float-float result res."""
+    x = _f32(x).reshape(-1)
+    yp = None
+    if y is not None:
+        y = _f32(y).reshape(-1); yp = _p(y)
+    rp = None
+    if res is not None:
+        res = _f32(res).reshape(2); rp = _p(res)
+    out = np.empty(4)
+    lib().exact_dot_f32(_p(x), yp, x.size, rp, _p(out))
+    return tuple(float(v) for v in out)
 
 
 def sqrt22(a):
@@ -176,6 +207,15 @@ def gemv_t(A, dY):
     k = dY.shape[0]
     dX = np.empty((k, n, 2), np.float32)
     lib().orc_gemv_t(_p(A), m, n, n, _p(dY), m, k, _p(dX), n); return dX
+
+
+def gemv_dA(dY, X):
+    """dA = dY X^T.  dY: (k, m, 2); X: (k, n, 2).  Returns dA as (m, n, 2)."""
+    dY = _f32(dY); X = _f32(X)
+    k, m = dY.shape[0], dY.shape[1]
+    n = X.shape[1]
+    dA = np.empty((m, n, 2), np.float32)
+    lib().orc_gemv_dA(_p(dY), m, m, _p(X), n, n, k, _p(dA), n); return dA
 
 
 def fp32_add(a, b):

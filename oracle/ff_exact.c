@@ -443,3 +443,31 @@ void exact_dot_ff(const float *x, const float *y, size_t n, const float *res, do
         out[3] = 0.0;
     }
 }
+
+/* Exact reference of a binary32 dot product (or sum when y is NULL), with
+ * the same outputs as exact_dot_ff: S as a binary128 (hi, lo) double pair,
+ * A = sum |x_i y_i|, E = (res[0] + res[1]) - S.  Every x_i y_i is exact in
+ * binary64. */
+void exact_dot_f32(const float *x, const float *y, size_t n, const float *res, double *out)
+{
+    static sacc s, sabs;
+    sa_clear(&s);
+    sa_clear(&sabs);
+    for (size_t i = 0; i < n; ++i) {
+        double p = y ? (double)x[i] * (double)y[i] : (double)x[i];
+        sa_add_double(&s, p);
+        sa_add_double(&sabs, fabs(p));
+    }
+    q128 S = sa_to_q128(&s);
+    double hi = (double)S;
+    out[0] = hi;
+    out[1] = (double)(S - (q128)hi);
+    out[2] = sa_to_double(&sabs);
+    if (res) {
+        sa_add_double(&s, -(double)res[0]);
+        sa_add_double(&s, -(double)res[1]);
+        out[3] = -sa_to_double(&s);
+    } else {
+        out[3] = 0.0;
+    }
+}

@@ -168,6 +168,58 @@ static void sqrt22(float ah, float al, float *rh, float *rl)
     add12(c, cc, rh, rl);
 }
 
+/* Fast2Sum (Dekker): s = a (+) b, t = (a + b) - s exactly when the exponent
+ * of a is at least that of b. */
+static void fast2sum(float a, float b, float *s_out, float *t_out)
+{
+    float s = a + b;
+    float z = s - a;
+    float t = b - z;
+    *s_out = s;
+    *t_out = t;
+}
+
+/* Weight gradient of Y = A X: dA = dY X^T, dA[r, j] = acc over c = 0 .. k-1
+ * of Add22(acc, Mul22(dY[r, c], X[j, c])).  dY: m x k column-major (lddy),
+ * X: n x k column-major (ldx), dA: m x n row-major (ldda). */
+void orc_gemv_dA(const float *dY, int64_t m, int64_t lddy, const float *X, int64_t n, int64_t ldx,
+                 int64_t k, float *dA, int64_t ldda)
+{
+    for (int64_t r = 0; r < m; ++r) {
+        for (int64_t j = 0; j < n; ++j) {
+            float h = 0.0f, l = 0.0f;
+            for (int64_t c = 0; c < k; ++c) {
+                const float *dy = &dY[2 * (c * lddy + r)];
+                const float *xv = &X[2 * (c * ldx + j)];
+                float ph, pl;
+                mul22(dy[0], dy[1], xv[0], xv[1], &ph, &pl);
+                add22(h, l, ph, pl, &h, &l);
+            }
+            dA[2 * (r * ldda + j)] = h;
+            dA[2 * (r * ldda + j) + 1] = l;
+        }
+    }
+}
+
+/* Accurate float-float addition (the paper's open problem of Add22's
+ * cancellation error, Sections 6.1 and 7): Algorithm 6 ("AccurateDWPlusDW")
+ * of Joldes, Muller and Popescu, "Tight and rigorous error bounds for basic
+ * building blocks of double-word arithmetic" (ACM TOMS 2017):
+ *   (sh, sl) = TwoSum(xh, yh); (th, tl) = TwoSum(xl, yl); c = sl + th;
+ *   (vh, vl) = Fast2Sum(sh, c); w = tl + vl; (zh, zl) = Fast2Sum(vh, w).
+ * Relative error <= 3u^2 / (1 - 4u), u = 2^-24, with no cancellation term.
+ * TwoSum is the paper's Add12. */
+static void add22_accurate(float xh, float xl, float yh, float yl, float *zh, float *zl)
+{
+    float sh, sl, th, tl, vh, vl;
+    add12(xh, yh, &sh, &sl);
+    add12(xl, yl, &th, &tl);
+    float c = sl + th;
+    fast2sum(sh, c, &vh, &vl);
+    float w = tl + vl;
+    fast2sum(vh, w, zh, zl);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Array entry points (called from the test harness through ctypes)          */
 /* ------------------------------------------------------------------------ */
@@ -313,6 +365,48 @@ void orc_gemv_t(const float *A, int64_t m, int64_t n, int64_t lda,
             dX[2 * (c * lddx + j) + 1] = l;
         }
     }
+}
+
+void orc_add22_accurate(const float *a, const float *b, float *r, size_t n)
+{
+    for (size_t i = 0; i < n; ++i)
+        add22_accurate(a[2 * i], a[2 * i + 1], b[2 * i], b[2 * i + 1], &r[2 * i], &r[2 * i + 1]);
+}
+
+/* Compensated summation and dot product of binary32 vectors (the
+ * "compensated algorithms" of Section 7): Ogita, Rump and Oishi, "Accurate
+ * sum and dot product" (SIAM J. Sci. Comput. 2005), Sum2 and Dot2, in their
+ * left-to-right order, with the paper's Add12 as TwoSum and the fused Mul12
+ * as TwoProduct.  The result is returned unrounded as the float-float value
+ * Add12(p, s) (equal to p + s exactly).
+ *   Sum2: p = x_0, s = 0; for i >= 1: (p, q) = TwoSum(p, x_i); s = s + q.
+ *   Dot2: (p, s) = TwoProduct(x_0, y_0); for i >= 1: (h, r) =
+ *         TwoProduct(x_i, y_i); (p, q) = TwoSum(p, h); s = s + (q + r). */
+void orc_sum2(const float *x, size_t n, float *out)
+{
+    float p = 0.0f, s = 0.0f;
+    if (n > 0)
+        p = x[0];
+    for (size_t i = 1; i < n; ++i) {
+        float q;
+        add12(p, x[i], &p, &q);
+        s = s + q;
+    }
+    add12(p, s, &out[0], &out[1]);
+}
+
+void orc_dot2(const float *x, const float *y, size_t n, float *out)
+{
+    float p = 0.0f, s = 0.0f;
+    if (n > 0)
+        mul12_fma(x[0], y[0], &p, &s);
+    for (size_t i = 1; i < n; ++i) {
+        float h, r, q;
+        mul12_fma(x[i], y[i], &h, &r);
+        add12(p, h, &p, &q);
+        s = s + (q + r);
+    }
+    add12(p, s, &out[0], &out[1]);
 }
 
 /* Plain binary32 operations, the normalisation baseline of the paper's

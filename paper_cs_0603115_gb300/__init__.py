@@ -24,8 +24,8 @@ from . import _lib
 from ._lib import FFError, ff2
 
 __all__ = [
-    "add12", "mul12", "add", "mul", "div", "sqrt", "axpy", "sum", "dot", "dot_backward",
-    "gemv", "gemv_t", "FFDot", "FFGemv", "ffdot", "ffgemv", "FFError", "workspace",
+    "add12", "mul12", "add", "add_accurate", "sum2", "dot2", "mul", "div", "sqrt", "axpy", "sum", "dot", "dot_backward",
+    "gemv", "gemv_t", "gemv_dA", "FFDot", "FFGemv", "ffdot", "ffgemv", "FFError", "workspace",
     "f64_add", "f64_mul", "f64_div", "f64_sqrt", "f64_dot", "f64_gemv", "f32_add", "f32_mul",
     "f32_mad", "load",
 ]
@@ -120,6 +120,12 @@ def add(a, b, out=None):
     return _binary("ff_add", a, b, out)
 
 
+def add_accurate(a, b, out=None):
+    """Accurate float-float a + b (Joldes-Muller-Popescu), relative error
+    <= 3 2^-48 / (1 - 2^-22) even under cancellation."""
+    return _binary("ff_add_accurate", a, b, out)
+
+
 def mul(a, b, out=None):
     """Mul22: float-float a * b."""
     return _binary("ff_mul", a, b, out)
@@ -180,6 +186,36 @@ def dot(x, y, out=None):
     return out
 
 
+def _f32_vec(t, name):
+    if not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+        raise ValueError(f"{name}: expected a contiguous float32 CUDA tensor")
+
+
+def sum2(x, out=None):
+    """Compensated Sum2 of a binary32 vector; returns the float-float (2,)
+    result on the device."""
+    _f32_vec(x, "ff_sum2")
+    if out is None:
+        out = torch.empty(2, dtype=torch.float32, device=x.device)
+    ws = _reduce_ws(x.numel(), x.device)
+    _lib.call("ff_sum2", _ptr(x), x.numel(), _ptr(out), _ptr(ws), ws.numel(), _stream())
+    return out
+
+
+def dot2(x, y, out=None):
+    """Compensated Dot2 of binary32 vectors; returns the float-float (2,)
+    result on the device."""
+    _f32_vec(x, "ff_dot2")
+    _f32_vec(y, "ff_dot2")
+    if x.numel() != y.numel():
+        raise ValueError("ff_dot2: size mismatch")
+    if out is None:
+        out = torch.empty(2, dtype=torch.float32, device=x.device)
+    ws = _reduce_ws(x.numel(), x.device)
+    _lib.call("ff_dot2", _ptr(x), _ptr(y), x.numel(), _ptr(out), _ptr(ws), ws.numel(), _stream())
+    return out
+
+
 def dot_backward(dout, x, y, dx=None, dy=None):
     """dx = Mul22(dout, y), dy = Mul22(dout, x); dout is a (2,) device tensor."""
     _check_ff(dout, "ff_dot_backward")
@@ -227,6 +263,21 @@ def gemv_t(A, dY, out=None):
     return out
 
 
+def gemv_dA(dY, X, out=None):
+    """dA = dY X^T (the weight gradient of Y = A X).  dY: (k, m, 2); X: (k, n, 2).
+    Returns dA as (m, n, 2) row-major."""
+    _check_ff(dY, "ff_gemv_dA")
+    _check_ff(X, "ff_gemv_dA")
+    if dY.dim() != 3 or X.dim() != 3 or dY.shape[0] != X.shape[0]:
+        raise ValueError("ff_gemv_dA: expected dY (k, m, 2) and X (k, n, 2)")
+    k, m = dY.shape[0], dY.shape[1]
+    n = X.shape[1]
+    if out is None:
+        out = torch.empty((m, n, 2), dtype=torch.float32, device=dY.device)
+    _lib.call("ff_gemv_dA", _ptr(dY), m, m, _ptr(X), n, n, k, _ptr(out), n, _stream())
+    return out
+
+
 # ---------------------------------------------------------------------------
 # autograd: hand-written adjoints
 # ---------------------------------------------------------------------------
@@ -250,17 +301,21 @@ class FFDot(torch.autograd.Function):
 
 
 class FFGemv(torch.autograd.Function):
-    """Y = A X with the adjoint dX = A^T dY (A is treated as a constant)."""
+    """Y = A X with the adjoints dX = A^T dY (ff_gemv_t) and, when A needs a
+    gradient, dA = dY X^T (ff_gemv_dA)."""
 
     @staticmethod
     def forward(ctx, A, X):
-        ctx.save_for_backward(A)
+        ctx.save_for_backward(A, X)
         return gemv(A, X)
 
     @staticmethod
     def backward(ctx, dY):
-        (A,) = ctx.saved_tensors
-        return None, gemv_t(A, dY.contiguous())
+        A, X = ctx.saved_tensors
+        dY = dY.contiguous()
+        dA = gemv_dA(dY, X) if ctx.needs_input_grad[0] else None
+        dX = gemv_t(A, dY) if ctx.needs_input_grad[1] else None
+        return dA, dX
 
 
 def ffdot(x, y):

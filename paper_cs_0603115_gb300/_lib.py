@@ -40,6 +40,11 @@ SIGNATURES = {
     "ff_mul12": (ST, [P, P, SZ, P]),
     "ff_add": (ST, [P, P, P, SZ, P]),
     "ff_mul": (ST, [P, P, P, SZ, P]),
+    "ff_add_accurate": (ST, [P, P, P, SZ, P]),
+    "ff_sum2": (ST, [P, SZ, P, P, SZ, P]),
+    "ff_dot2": (ST, [P, P, SZ, P, P, SZ, P]),
+    "ff_reduce2_launch_shape": (ST, [P, P, SZ, ctypes.POINTER(ctypes.c_uint), ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(ctypes.c_int)]),
     "ff_div": (ST, [P, P, P, SZ, P]),
     "ff_sqrt": (ST, [P, P, SZ, P]),
     "ff_axpy": (ST, [ff2, P, P, P, SZ, P]),
@@ -53,6 +58,7 @@ SIGNATURES = {
     "ff_gemv": (ST, [P, I64, I64, I64, P, I64, I64, P, I64, P]),
     "ff_gemv_t_workspace_bytes": (SZ, [I64, I64, I64]),
     "ff_gemv_t": (ST, [P, I64, I64, I64, P, I64, I64, P, I64, P, SZ, P]),
+    "ff_gemv_dA": (ST, [P, I64, I64, P, I64, I64, I64, P, I64, P]),
     "ff_f64_add": (ST, [P, P, P, SZ, P]),
     "ff_f64_mul": (ST, [P, P, P, SZ, P]),
     "ff_f64_div": (ST, [P, P, P, SZ, P]),
@@ -96,7 +102,7 @@ def declared_symbols() -> list[str]:
     """Every function name declared in include/ff.h."""
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(ff_[a-z0-9_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(ff_[A-Za-z0-9_]+)\s*\(", text)))
 
 
 def load() -> ctypes.CDLL:

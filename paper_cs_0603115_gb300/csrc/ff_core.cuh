@@ -85,4 +85,27 @@ __device__ __forceinline__ float2 sqrt22(float2 a)
     return make_float2(z ? a.x : r.x, z ? 0.0f : r.y);
 }
 
+// Fast2Sum (Dekker): s = a (+) b, t = (a + b) - s exactly when the exponent
+// of a is at least that of b.
+__device__ __forceinline__ float2 fast2sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float z = __fsub_rn(s, a);
+    return make_float2(s, __fsub_rn(b, z));
+}
+
+// Accurate float-float addition (Joldes, Muller and Popescu 2017,
+// Algorithm 6): the two TwoSums of the high and the low parts, then two
+// Fast2Sum renormalisations.  Relative error <= 3u^2 / (1 - 4u) (u = 2^-24)
+// even under cancellation, where Add22 only bounds the error by 2^-24 |al + bl|.
+__device__ __forceinline__ float2 add22_accurate(float2 x, float2 y)
+{
+    const float2 s = add12(x.x, y.x);
+    const float2 t = add12(x.y, y.y);
+    const float c = __fadd_rn(s.y, t.x);
+    const float2 v = fast2sum(s.x, c);
+    const float w = __fadd_rn(t.y, v.y);
+    return fast2sum(v.x, w);
+}
+
 }  // namespace ffk

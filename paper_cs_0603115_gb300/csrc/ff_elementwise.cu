@@ -19,6 +19,9 @@ struct OpMul12 {
 struct OpAdd22 {
     __device__ void operator()(const float2 (&x)[2], float2 (&y)[1]) const { y[0] = ffk::add22(x[0], x[1]); }
 };
+struct OpAdd22Acc {
+    __device__ void operator()(const float2 (&x)[2], float2 (&y)[1]) const { y[0] = ffk::add22_accurate(x[0], x[1]); }
+};
 struct OpMul22 {
     __device__ void operator()(const float2 (&x)[2], float2 (&y)[1]) const { y[0] = ffk::mul22(x[0], x[1]); }
 };
@@ -112,6 +115,12 @@ ff_status ff_add(const ff2* a, const ff2* b, ff2* out, size_t n, cudaStream_t s)
 {
     return run2<float2, OpAdd22>(reinterpret_cast<const float2*>(a), reinterpret_cast<const float2*>(b),
                                  reinterpret_cast<float2*>(out), n, s);
+}
+
+ff_status ff_add_accurate(const ff2* a, const ff2* b, ff2* out, size_t n, cudaStream_t s)
+{
+    return run2<float2, OpAdd22Acc>(reinterpret_cast<const float2*>(a), reinterpret_cast<const float2*>(b),
+                                    reinterpret_cast<float2*>(out), n, s);
 }
 
 ff_status ff_mul(const ff2* a, const ff2* b, ff2* out, size_t n, cudaStream_t s)

@@ -202,18 +202,83 @@ void launch_gemv_t_tile(const float2* A, int64_t m, int64_t n, int64_t lda, cons
     }
 }
 
-// Number of row blocks for the adjoint: enough blocks to fill the GPU a few
-// times over, each row block at least 64 rows long.
-int64_t row_blocks(int64_t m, int64_t n, int sm_count)
+const void* gemv_t_kernel_ptr(int kt, bool vec)
 {
-    const int64_t col_blocks = (n / 2 + kGBlock - 1) / kGBlock;
-    int64_t want = (static_cast<int64_t>(sm_count) * 4 + col_blocks - 1) / (col_blocks > 0 ? col_blocks : 1);
-    if (want < 1) want = 1;
-    int64_t maxrb = m / 64;
+    switch (kt) {
+    case 16: return vec ? reinterpret_cast<const void*>(&gemv_t_kernel<16, true>)
+                        : reinterpret_cast<const void*>(&gemv_t_kernel<16, false>);
+    case 8: return vec ? reinterpret_cast<const void*>(&gemv_t_kernel<8, true>)
+                       : reinterpret_cast<const void*>(&gemv_t_kernel<8, false>);
+    case 4: return vec ? reinterpret_cast<const void*>(&gemv_t_kernel<4, true>)
+                       : reinterpret_cast<const void*>(&gemv_t_kernel<4, false>);
+    case 2: return vec ? reinterpret_cast<const void*>(&gemv_t_kernel<2, true>)
+                       : reinterpret_cast<const void*>(&gemv_t_kernel<2, false>);
+    default: return vec ? reinterpret_cast<const void*>(&gemv_t_kernel<1, true>)
+                        : reinterpret_cast<const void*>(&gemv_t_kernel<1, false>);
+    }
+}
+
+// Number of row blocks for the adjoint.  The grid is col_blocks x nrb blocks;
+// nrb is chosen so that the grid fills whole waves of resident blocks (SMs x
+// blocks per SM of the widest tile's kernel): the adjoint is FP32-issue
+// bound for k > 2, and a last, partly filled wave would idle most SMs.
+// Every row block keeps at least 32 rows; at most 64 row blocks.
+int64_t row_blocks(int64_t m, int64_t n, int64_t k, bool vec, int sm_count)
+{
+    const int64_t cols = vec ? n / 2 : n;
+    const int64_t col_blocks = (cols + kGBlock - 1) / kGBlock;
+    if (col_blocks < 1 || m < 64) return 1;
+    const int occ = ffh::occupancy(gemv_t_kernel_ptr(tile_for(k), vec), kGBlock);
+    const int64_t resident = static_cast<int64_t>(sm_count) * (occ > 0 ? occ : 1);
+    int64_t maxrb = m / 32;
+    if (maxrb > 64) maxrb = 64;
     if (maxrb < 1) maxrb = 1;
-    if (want > maxrb) want = maxrb;
-    if (want > 64) want = 64;
-    return want;
+    int64_t best = 1;
+    double best_eff = -1.0;
+    for (int64_t nrb = 1; nrb <= maxrb; ++nrb) {
+        const int64_t blocks = nrb * col_blocks;
+        const int64_t waves = (blocks + resident - 1) / resident;
+        double eff = static_cast<double>(blocks) / static_cast<double>(waves * resident);
+        if (blocks < resident) eff *= 0.999;  // prefer at least one full wave when possible
+        if (eff > best_eff + 1e-3) {
+            best_eff = eff;
+            best = nrb;
+        }
+    }
+    return best;
+}
+
+// ---------------------------------------------------------------------------
+// dA = dY X^T: one thread per pair of adjacent columns j of one row r of dA
+// (coalesced 16-byte loads of X and stores of dA along the row); the k terms
+// of each element are accumulated in order c = 0 .. k-1, so the result is
+// the oracle's left-to-right sum bit for bit.  dY[r, c] is a warp-uniform
+// broadcast load.
+// ---------------------------------------------------------------------------
+template <bool VEC>
+__global__ void __launch_bounds__(kGBlock)
+gemv_dA_kernel(const float2* __restrict__ dY, int64_t m, int64_t lddy, const float2* __restrict__ X, int64_t n,
+               int64_t ldx, int64_t k, float2* __restrict__ dA, int64_t ldda)
+{
+    const int64_t r = blockIdx.y;
+    if (VEC) {
+        const int64_t jp = static_cast<int64_t>(blockIdx.x) * kGBlock + threadIdx.x;
+        if (2 * jp >= n) return;
+        float2 acc0 = make_float2(0.0f, 0.0f), acc1 = make_float2(0.0f, 0.0f);
+        for (int64_t c = 0; c < k; ++c) {
+            const float2 d = __ldg(dY + c * lddy + r);
+            const float4 x = __ldg(reinterpret_cast<const float4*>(X + c * ldx) + jp);
+            acc0 = ffk::add22(acc0, ffk::mul22(d, make_float2(x.x, x.y)));
+            acc1 = ffk::add22(acc1, ffk::mul22(d, make_float2(x.z, x.w)));
+        }
+        __stcs(reinterpret_cast<float4*>(dA + r * ldda) + jp, make_float4(acc0.x, acc0.y, acc1.x, acc1.y));
+    } else {
+        const int64_t j = static_cast<int64_t>(blockIdx.x) * kGBlock + threadIdx.x;
+        if (j >= n) return;
+        float2 acc = make_float2(0.0f, 0.0f);
+        for (int64_t c = 0; c < k; ++c) acc = ffk::add22(acc, ffk::mul22(__ldg(dY + c * lddy + r), X[c * ldx + j]));
+        dA[r * ldda + j] = acc;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -249,9 +314,9 @@ gemv_f64_kernel(const double* __restrict__ A, int64_t m, int64_t n, int64_t lda,
 
 bool bad_dims(int64_t m, int64_t n, int64_t k) { return m < 0 || n < 0 || k < 1 || k > kMaxK; }
 
-size_t gemv_t_ws(int64_t m, int64_t n, int64_t k, int sm_count)
+size_t gemv_t_ws(int64_t m, int64_t n, int64_t k, bool vec, int sm_count)
 {
-    const int64_t nrb = row_blocks(m, n, sm_count);
+    const int64_t nrb = row_blocks(m, n, k, vec, sm_count);
     if (nrb <= 1) return 16;
     return static_cast<size_t>(nrb) * static_cast<size_t>(n) * static_cast<size_t>(k) * sizeof(float2);
 }
@@ -295,7 +360,10 @@ size_t ff_gemv_t_workspace_bytes(int64_t m, int64_t n, int64_t k)
     if (bad_dims(m, n, k)) return 0;
     ffh::DeviceInfo di;
     if (ffh::device_info(&di) != FF_OK) return 0;
-    return gemv_t_ws(m, n, k, di.sm_count);
+    // the workspace must cover either access path: take the larger
+    const size_t a = gemv_t_ws(m, n, k, true, di.sm_count);
+    const size_t b = gemv_t_ws(m, n, k, false, di.sm_count);
+    return a > b ? a : b;
 }
 
 ff_status ff_gemv_t(const ff2* A_, int64_t m, int64_t n, int64_t lda, const ff2* dY_, int64_t lddy, int64_t k,
@@ -312,15 +380,15 @@ ff_status ff_gemv_t(const ff2* A_, int64_t m, int64_t n, int64_t lda, const ff2*
     auto* A = reinterpret_cast<const float2*>(A_);
     auto* dY = reinterpret_cast<const float2*>(dY_);
     auto* dX = reinterpret_cast<float2*>(dX_);
-    const int64_t nrb = row_blocks(m, n, di.sm_count);
+    const bool vec = (n % 2 == 0) && (lda % 2 == 0) && ffh::aligned(A, 16);
+    const int64_t nrb = row_blocks(m, n, k, vec, di.sm_count);
     const int64_t rpb = m > 0 ? (m + nrb - 1) / nrb : 0;
     float2* part = nullptr;
     if (nrb > 1) {
-        if (ws == nullptr || ws_bytes < gemv_t_ws(m, n, k, di.sm_count) || !ffh::aligned(ws, 16))
+        if (ws == nullptr || ws_bytes < gemv_t_ws(m, n, k, vec, di.sm_count) || !ffh::aligned(ws, 16))
             return FF_ERR_WORKSPACE;
         part = static_cast<float2*>(ws);
     }
-    const bool vec = (n % 2 == 0) && (lda % 2 == 0) && ffh::aligned(A, 16);
     for (int64_t c0 = 0; c0 < k;) {
         const int kt = tile_for(k - c0);
         const float2* dYc = dY + c0 * lddy;
@@ -348,6 +416,29 @@ ff_status ff_gemv_t(const ff2* A_, int64_t m, int64_t n, int64_t lda, const ff2*
         if (st != FF_OK) return st;
     }
     return FF_OK;
+}
+
+ff_status ff_gemv_dA(const ff2* dY_, int64_t m, int64_t lddy, const ff2* X_, int64_t n, int64_t ldx, int64_t k,
+                     ff2* dA_, int64_t ldda, cudaStream_t s)
+{
+    if (bad_dims(m, n, k) || lddy < m || ldx < n || ldda < n) return FF_ERR_INVALID_ARG;
+    if (m > 2147483647) return FF_ERR_INVALID_ARG;  // one grid row per row of dA
+    const size_t an = static_cast<size_t>(m) * static_cast<size_t>(n);
+    if (!ffh::ok_ptr(dY_, static_cast<size_t>(m)) || !ffh::ok_ptr(X_, static_cast<size_t>(n)) || !ffh::ok_ptr(dA_, an))
+        return FF_ERR_INVALID_ARG;
+    if (m == 0 || n == 0) return FF_OK;
+    auto* dY = reinterpret_cast<const float2*>(dY_);
+    auto* X = reinterpret_cast<const float2*>(X_);
+    auto* dA = reinterpret_cast<float2*>(dA_);
+    const bool vec = (n % 2 == 0) && (ldx % 2 == 0) && (ldda % 2 == 0) && ffh::aligned(X, 16) && ffh::aligned(dA, 16);
+    if (vec) {
+        dim3 grid(static_cast<unsigned>((n / 2 + kGBlock - 1) / kGBlock), static_cast<unsigned>(m));
+        gemv_dA_kernel<true><<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, k, dA, ldda);
+    } else {
+        dim3 grid(static_cast<unsigned>((n + kGBlock - 1) / kGBlock), static_cast<unsigned>(m));
+        gemv_dA_kernel<false><<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, k, dA, ldda);
+    }
+    return ffh::check_launch();
 }
 
 ff_status ff_f64_gemv(const double* A, int64_t m, int64_t n, int64_t lda, const double* X, int64_t ldx, int64_t k,

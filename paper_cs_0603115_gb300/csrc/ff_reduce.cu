@@ -33,6 +33,7 @@ struct FFSum {
     using T = float2;
     using Acc = float2;
     static constexpr bool kDot = false;
+    __device__ static Acc finalize(Acc a) { return a; }
     __device__ static Acc zero() { return make_float2(0.0f, 0.0f); }
     __device__ static Acc step(Acc acc, T x, T) { return ffk::add22(acc, x); }
     __device__ static Acc combine(Acc a, Acc b) { return ffk::add22(a, b); }
@@ -51,20 +52,60 @@ struct F64Dot {
     using T = double;
     using Acc = double;
     static constexpr bool kDot = true;
+    __device__ static Acc finalize(Acc a) { return a; }
     __device__ static Acc zero() { return 0.0; }
     __device__ static Acc step(Acc acc, T x, T y) { return __fma_rn(x, y, acc); }
     __device__ static Acc combine(Acc a, Acc b) { return __dadd_rn(a, b); }
     __device__ static Acc shfl_down(Acc v, int off) { return __shfl_down_sync(0xffffffffu, v, off); }
 };
 
+// Compensated Sum2 / Dot2 of binary32 vectors (Ogita, Rump and Oishi 2005)
+// with the accumulator (p, s): p the running sum, s the running sum of the
+// exact errors.  Step: (h, r) = TwoProduct(x, y); (p, q) = TwoSum(p, h);
+// s = s + (q + r) (Sum2: h = x, r = 0).  Two accumulators combine as
+// (p, q) = TwoSum(a.p, b.p); s = a.s + (b.s + q).  The result is the
+// float-float Add12(p, s), equal to p + s exactly.
+struct F32Sum2 {
+    using T = float;
+    using Acc = float2;  // (p, s)
+    static constexpr bool kDot = false;
+    __device__ static Acc zero() { return make_float2(0.0f, 0.0f); }
+    __device__ static Acc step(Acc a, T x, T)
+    {
+        const float2 pq = ffk::add12(a.x, x);
+        return make_float2(pq.x, __fadd_rn(a.y, pq.y));
+    }
+    __device__ static Acc combine(Acc a, Acc b)
+    {
+        const float2 pq = ffk::add12(a.x, b.x);
+        return make_float2(pq.x, __fadd_rn(a.y, __fadd_rn(b.y, pq.y)));
+    }
+    __device__ static Acc finalize(Acc a) { return ffk::add12(a.x, a.y); }
+    __device__ static Acc shfl_down(Acc v, int off)
+    {
+        return make_float2(__shfl_down_sync(0xffffffffu, v.x, off), __shfl_down_sync(0xffffffffu, v.y, off));
+    }
+};
+
+struct F32Dot2 : F32Sum2 {
+    static constexpr bool kDot = true;
+    __device__ static Acc step(Acc a, T x, T y)
+    {
+        const float2 hr = ffk::mul12(x, y);
+        const float2 pq = ffk::add12(a.x, hr.x);
+        return make_float2(pq.x, __fadd_rn(a.y, __fadd_rn(pq.y, hr.y)));
+    }
+};
+
 template <typename T> struct V16;
-template <> struct V16<float2> { using V = float4; };
-template <> struct V16<double> { using V = double2; };
+template <> struct V16<float2> { using V = float4; static constexpr int E = 2; };
+template <> struct V16<double> { using V = double2; static constexpr int E = 2; };
+template <> struct V16<float> { using V = float4; static constexpr int E = 4; };
 
 template <typename T>
 union Pack2 {
     typename V16<T>::V v;
-    T e[2];
+    T e[V16<T>::E];
 };
 
 // Steps 2-3: the block's combined value ends in thread 0.
@@ -97,13 +138,15 @@ reduce_kernel(const typename P::T* x, const typename P::T* y, size_t n, int head
     __shared__ Acc sm[kRWarps];
     __shared__ bool is_last;
 
+    constexpr int E = V16<T>::E;
     const size_t tid = static_cast<size_t>(blockIdx.x) * kRBlock + threadIdx.x;
     const size_t nthr = static_cast<size_t>(gridDim.x) * kRBlock;
     const size_t h = static_cast<size_t>(head);
-    const size_t nv = (n - h) / 2;
+    const size_t nv = (n - h) / E;
 
     Acc acc = P::zero();
-    if (tid == 0 && h == 1) acc = P::step(acc, x[0], P::kDot ? y[0] : T());
+    if (tid == 0)
+        for (size_t j = 0; j < h; ++j) acc = P::step(acc, x[j], P::kDot ? y[j] : T());
 
     const V* xv = reinterpret_cast<const V*>(x + h);
     const V* yv = reinterpret_cast<const V*>((P::kDot ? y : x) + h);
@@ -116,23 +159,23 @@ reduce_kernel(const typename P::T* x, const typename P::T* y, size_t n, int head
             if (P::kDot) ys[u].v = __ldcs(yv + i + u * nthr);
         }
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            acc = P::step(acc, xs[u].e[0], P::kDot ? ys[u].e[0] : T());
-            acc = P::step(acc, xs[u].e[1], P::kDot ? ys[u].e[1] : T());
-        }
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int e = 0; e < E; ++e) acc = P::step(acc, xs[u].e[e], P::kDot ? ys[u].e[e] : T());
     }
     for (; i < nv; i += nthr) {
         Pack2<T> xs, ys;
         xs.v = __ldcs(xv + i);
         if (P::kDot) ys.v = __ldcs(yv + i);
-        acc = P::step(acc, xs.e[0], P::kDot ? ys.e[0] : T());
-        acc = P::step(acc, xs.e[1], P::kDot ? ys.e[1] : T());
+#pragma unroll
+        for (int e = 0; e < E; ++e) acc = P::step(acc, xs.e[e], P::kDot ? ys.e[e] : T());
     }
-    if (tid == 0 && ((n - h) & 1)) acc = P::step(acc, x[n - 1], P::kDot ? y[n - 1] : T());
+    if (tid == 0)
+        for (size_t j = h + nv * E; j < n; ++j) acc = P::step(acc, x[j], P::kDot ? y[j] : T());
 
     acc = block_reduce<P>(acc, sm);
     if (gridDim.x == 1) {
-        if (threadIdx.x == 0) *out = acc;
+        if (threadIdx.x == 0) *out = P::finalize(acc);
         return;
     }
     if (threadIdx.x == 0) {
@@ -148,7 +191,7 @@ reduce_kernel(const typename P::T* x, const typename P::T* y, size_t n, int head
     for (unsigned b = threadIdx.x; b < gridDim.x; b += kRBlock) a2 = P::combine(a2, __ldcg(partials + b));
     a2 = block_reduce<P>(a2, sm);
     if (threadIdx.x == 0) {
-        *out = a2;
+        *out = P::finalize(a2);
         *ticket = 0u;
     }
 }
@@ -169,7 +212,7 @@ reduce_scalar_kernel(const typename P::T* x, const typename P::T* y, size_t n, t
     for (size_t i = tid; i < n; i += nthr) acc = P::step(acc, x[i], P::kDot ? y[i] : T());
     acc = block_reduce<P>(acc, sm);
     if (gridDim.x == 1) {
-        if (threadIdx.x == 0) *out = acc;
+        if (threadIdx.x == 0) *out = P::finalize(acc);
         return;
     }
     if (threadIdx.x == 0) {
@@ -185,7 +228,7 @@ reduce_scalar_kernel(const typename P::T* x, const typename P::T* y, size_t n, t
     for (unsigned b = threadIdx.x; b < gridDim.x; b += kRBlock) a2 = P::combine(a2, __ldcg(partials + b));
     a2 = block_reduce<P>(a2, sm);
     if (threadIdx.x == 0) {
-        *out = a2;
+        *out = P::finalize(a2);
         *ticket = 0u;
     }
 }
@@ -212,11 +255,13 @@ Shape shape_for(const typename P::T* x, const typename P::T* y, size_t n, const 
     sh.vec = (px == py) && (px % sizeof(T) == 0);
     const size_t cap = max_blocks(di);
     if (sh.vec) {
-        sh.head = (px != 0 && n > 0) ? 1 : 0;
+        constexpr int E = V16<T>::E;
+        sh.head = px != 0 ? static_cast<int>((16u - px) / sizeof(T)) : 0;
+        if (static_cast<size_t>(sh.head) > n) sh.head = static_cast<int>(n);
         const void* kern = reinterpret_cast<const void*>(&reduce_kernel<P, kU>);
         int occ = ffh::occupancy(kern, kRBlock);
         if (occ > kRMaxBlocksPerSm) occ = kRMaxBlocksPerSm;
-        const size_t nv = n > static_cast<size_t>(sh.head) ? (n - sh.head) / 2 : 0;
+        const size_t nv = n > static_cast<size_t>(sh.head) ? (n - sh.head) / E : 0;
         sh.grid = ffh::grid_for(nv, static_cast<size_t>(kRBlock) * kU, di.sm_count, occ);
     } else {
         sh.head = 0;
@@ -234,7 +279,8 @@ ff_status run_reduce(const typename P::T* x, const typename P::T* y, size_t n, t
                      size_t ws_bytes, cudaStream_t s)
 {
     using T = typename P::T;
-    if (!ffh::ok_ptr(x, n) || (P::kDot && !ffh::ok_ptr(y, n))) return FF_ERR_INVALID_ARG;
+    auto ok_in = [n](const void* p) { return n == 0 || (p != nullptr && ffh::aligned(p, sizeof(T))); };
+    if (!ok_in(x) || (P::kDot && !ok_in(y))) return FF_ERR_INVALID_ARG;
     if (!ffh::ok_ptr(out, 1)) return FF_ERR_INVALID_ARG;
     ffh::DeviceInfo di;
     ff_status st = ffh::device_info(&di);
@@ -291,6 +337,33 @@ ff_status ff_dot(const ff2* x, const ff2* y, size_t n, ff2* out_dev, void* ws, s
 {
     return run_reduce<FFDot>(reinterpret_cast<const float2*>(x), reinterpret_cast<const float2*>(y), n,
                              reinterpret_cast<float2*>(out_dev), ws, ws_bytes, s);
+}
+
+ff_status ff_sum2(const float* x, size_t n, ff2* out_dev, void* ws, size_t ws_bytes, cudaStream_t s)
+{
+    if (!(n == 0 || (x != nullptr && ffh::aligned(x, 4)))) return FF_ERR_INVALID_ARG;
+    return run_reduce<F32Sum2>(x, nullptr, n, reinterpret_cast<float2*>(out_dev), ws, ws_bytes, s);
+}
+
+ff_status ff_dot2(const float* x, const float* y, size_t n, ff2* out_dev, void* ws, size_t ws_bytes,
+                  cudaStream_t s)
+{
+    if (!(n == 0 || (x != nullptr && y != nullptr && ffh::aligned(x, 4) && ffh::aligned(y, 4))))
+        return FF_ERR_INVALID_ARG;
+    return run_reduce<F32Dot2>(x, y, n, reinterpret_cast<float2*>(out_dev), ws, ws_bytes, s);
+}
+
+ff_status ff_reduce2_launch_shape(const float* x, const float* y, size_t n, unsigned* grid, int* head, int* vector)
+{
+    if (!grid || !head || !vector) return FF_ERR_INVALID_ARG;
+    ffh::DeviceInfo di;
+    ff_status st = ffh::device_info(&di);
+    if (st != FF_OK) return st;
+    Shape sh = y ? shape_for<F32Dot2>(x, y, n, di) : shape_for<F32Sum2>(x, nullptr, n, di);
+    *grid = sh.grid;
+    *head = sh.head;
+    *vector = sh.vec ? 1 : 0;
+    return FF_OK;
 }
 
 ff_status ff_f64_dot(const double* x, const double* y, size_t n, double* out_dev, void* ws, size_t ws_bytes,

@@ -5,8 +5,14 @@
 // for the native baselines).  The body moves 16-byte vectors (two float2,
 // two double, four float) with evict-first streaming loads and stores: every
 // byte is touched once, so nothing is worth keeping in L1/L2.  Each thread
-// issues U vector loads per input before computing, which keeps
-// U x NIN x 16 bytes per thread in flight to cover HBM latency.
+// issues U vector loads per input before computing.
+//
+// Residency: a GB300 sustains the highest read+write DRAM throughput on these
+// kernels with about 40-50 KB of loads in flight per SM, not with every SM
+// full: measured on 2^28 values, Add22 reaches ~7.0 TB/s with U = 2 and 3
+// blocks of 256 per SM against ~6.6 TB/s at full occupancy, and the
+// one-input kernels ~6.6 TB/s with U = 2 and 5 blocks per SM.  The launcher
+// therefore caps the grid at SMs x kBlocksPerSm[NIN].
 //
 // Alignment: device arrays are only required to be aligned to sizeof(T).
 // If all arrays share the same offset modulo 16 bytes, a scalar head of
@@ -146,9 +152,12 @@ __global__ void __launch_bounds__(kBlock) stream_scalar(Args<T, NIN, NOUT> a, Op
     for (; i < a.n; i += nthr) scalar_at(a, op, i);
 }
 
+// Resident 256-thread blocks per SM by number of input arrays (see above).
+constexpr int blocks_per_sm(int nin) { return nin == 1 ? 5 : nin == 2 ? 3 : 2; }
+
 // Host launcher: validates nothing (the caller did), picks the path and the
 // grid, launches on `s`.
-template <typename T, int NIN, int NOUT, class Op, int U = 4>
+template <typename T, int NIN, int NOUT, class Op, int U = 2>
 ff_status launch(Args<T, NIN, NOUT> a, Op op, cudaStream_t s)
 {
     if (a.n == 0) return FF_OK;
@@ -166,14 +175,16 @@ ff_status launch(Args<T, NIN, NOUT> a, Op op, cudaStream_t s)
         if (head > a.n) head = a.n;
         a.head = static_cast<int>(head);
         const void* kern = reinterpret_cast<const void*>(&stream_vec<T, NIN, NOUT, Op, U>);
-        const int occ = ffh::occupancy(kern, kBlock);
+        int occ = ffh::occupancy(kern, kBlock);
+        if (occ > blocks_per_sm(NIN)) occ = blocks_per_sm(NIN);
         const size_t nv = (a.n - head) / E;
         unsigned grid = ffh::grid_for(nv > 0 ? nv : 1, static_cast<size_t>(kBlock) * U, di.sm_count, occ);
         stream_vec<T, NIN, NOUT, Op, U><<<grid, kBlock, 0, s>>>(a, op);
     } else {
         a.head = 0;
         const void* kern = reinterpret_cast<const void*>(&stream_scalar<T, NIN, NOUT, Op, U>);
-        const int occ = ffh::occupancy(kern, kBlock);
+        int occ = ffh::occupancy(kern, kBlock);
+        if (occ > 2 * blocks_per_sm(NIN)) occ = 2 * blocks_per_sm(NIN);
         unsigned grid = ffh::grid_for(a.n, static_cast<size_t>(kBlock) * U, di.sm_count, occ);
         stream_scalar<T, NIN, NOUT, Op, U><<<grid, kBlock, 0, s>>>(a, op);
     }

@@ -177,6 +177,65 @@ def ill_dot(n: int, cond: float, seed: int, device="cpu") -> IllDot:
                   cond_target=float(cond), dot_design=float(T))
 
 
+def _mant24(n: int, g: torch.Generator, device) -> torch.Tensor:
+    """Random binary32-representable values with 24-bit significands in
+    [0.5, 1) and random signs (as binary64)."""
+    m = torch.randint(2 ** 23, 2 ** 24, (n,), generator=g, device=device).to(torch.float64)
+    s = torch.randint(0, 2, (n,), generator=g, device=device).to(torch.float64)
+    return (2.0 * s - 1.0) * m * 2.0 ** -24
+
+
+@dataclass
+class IllDotF32:
+    x: torch.Tensor          # (n,) binary32
+    y: torch.Tensor          # (n,) binary32
+    cond_target: float
+    dot_design: float
+
+
+def ill_dot_f32(n: int, cond: float, seed: int, device="cpu") -> IllDotF32:
+    """The ill-conditioned dot of ``ill_dot`` for plain binary32 vectors (the
+    inputs of the compensated Sum2 / Dot2): same construction, every value a
+    binary32 number, so every product x_i y_i is exact in binary64 and the
+    design sum is formed from exact products."""
+    if n < 4:
+        raise ValueError("ill_dot_f32 needs n >= 4")
+    g = _gen(seed, device)
+    E = max(0, int(round(math.log2(cond) / 2)))
+    h = n // 2
+    m = n - h
+    e1 = torch.randint(0, E + 1, (h,), generator=g, device=device).to(torch.float64)
+    x1 = _mant24(h, g, device) * torch.exp2(e1)
+    y1 = _mant24(h, g, device) * torch.exp2(e1)
+    p1 = x1 * y1
+    perm = torch.randperm(h, generator=g, device=device)
+    if m > h:
+        perm = torch.cat([perm, perm[:1]])
+    e2 = torch.randint(0, E + 1, (m,), generator=g, device=device).to(torch.float64)
+    x2 = _mant24(m, g, device) * torch.exp2(e2)
+    y2 = (-(p1[perm] / x2)).to(torch.float32).to(torch.float64)
+    x = torch.cat([x1, x2])
+    y = torch.cat([y1, y2])
+    prod = x * y                                              # exact
+    rest_s = prod[:-1].sum().item()
+    rest_a = prod[:-1].abs().sum().item()
+    sgn = 1.0 if rest_s >= 0 else -1.0
+    t_abs = 2.0 * (rest_a - abs(rest_s)) / (cond - 2.0) if cond > 2 else abs(rest_s) + rest_a
+    if t_abs < abs(rest_s):
+        t_abs = 2.0 * (rest_a + abs(rest_s)) / (cond + 2.0)
+    T = sgn * t_abs
+    need = T - rest_s
+    el = max(0, int(round(math.log2(abs(need)) / 2))) if need != 0 else 0
+    x_last = (_mant24(1, g, device) * 2.0 ** el)[0]
+    x = x.clone()
+    y = y.clone()
+    x[-1] = x_last
+    y[-1] = float(torch.tensor(need / float(x_last), dtype=torch.float64).to(torch.float32))
+    order = torch.randperm(n, generator=g, device=device)
+    return IllDotF32(x=x[order].to(torch.float32).contiguous(), y=y[order].to(torch.float32).contiguous(),
+                     cond_target=float(cond), dot_design=float(T))
+
+
 @dataclass
 class GemvInputs:
     A: torch.Tensor   # (m, n, 2) row-major float-float

@@ -1,0 +1,90 @@
+"""Parity of the rows beyond the paper's operator set: the accurate
+float-float addition (bit-exact against the oracle) and the compensated
+Sum2 / Dot2 of binary32 vectors (bit-exact against a replay of the
+documented order, within the error bound of the exact value)."""
+import ctypes
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_cs_0603115_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+
+
+def same_bits(got, want):
+    got = np.ascontiguousarray(got, np.float32)
+    want = np.ascontiguousarray(want, np.float32)
+    nan = np.isnan(got) & np.isnan(want)
+    eq = (got.view(np.uint32) == want.view(np.uint32)) | nan
+    assert eq.all(), f"{(~eq).sum()} mismatches"
+
+
+@pytest.mark.parametrize("n", [0, 1, 3, 4099, 1 << 20])
+@pytest.mark.parametrize("offset", [0, 1])
+def test_add_accurate_bitexact(n, offset):
+    import paper_cs_0603115_gb300 as ff
+    e = inputs.elementwise(n + 1, inputs.seed_for(0, 30), cancel_frac=0.3)
+    a = e.a.to(DEV)[offset:offset + n]
+    b = e.b.to(DEV)[offset:offset + n]
+    same_bits(ff.add_accurate(a, b).cpu().numpy(), oracle.add22_accurate(a.cpu().numpy(), b.cpu().numpy()))
+
+
+def test_add_accurate_specials():
+    import paper_cs_0603115_gb300 as ff
+    vals = [0.0, -0.0, 1.0, -1.0, 2.0 ** -149, 1e38, -1e38, np.inf, -np.inf, np.nan, 3.0, 2.0 ** -100]
+    lo = [0.0, 2.0 ** -149, -1e-20]
+    a = np.array([(h, l) for h in vals for l in lo], np.float32)
+    A = np.repeat(a, len(a), axis=0)
+    B = np.tile(a, (len(a), 1))
+    got = ff.add_accurate(torch.from_numpy(A).to(DEV), torch.from_numpy(B).to(DEV)).cpu().numpy()
+    same_bits(got, oracle.add22_accurate(A, B))
+
+
+def _shape(x, y):
+    from paper_cs_0603115_gb300 import _lib
+    g, h, v = ctypes.c_uint(), ctypes.c_int(), ctypes.c_int()
+    _lib.call("ff_reduce2_launch_shape", x.data_ptr(), None if y is None else y.data_ptr(), x.numel(),
+              ctypes.byref(g), ctypes.byref(h), ctypes.byref(v))
+    return g.value, h.value, bool(v.value)
+
+
+@pytest.mark.parametrize("n", [0, 1, 5, 1001, 70003, 1 << 20])
+@pytest.mark.parametrize("offset", [0, 1, 3])
+def test_dot2_sum2_replay_bitexact(n, offset):
+    import paper_cs_0603115_gb300 as ff
+    import replay
+    g = inputs.ill_dot_f32(max(n, 4) + 3, 1e9, inputs.seed_for(5, 50 + n % 7))
+    x = g.x.to(DEV)[offset:offset + n]
+    y = g.y.to(DEV)[offset:offset + n]
+    xn, yn = x.cpu().numpy(), y.cpu().numpy()
+    pol = replay.Dot2Policy()
+    gr, h, v = _shape(x, y)
+    terms = oracle.mul12(np.stack([xn, yn], 1)) if n else np.zeros((0, 2), np.float32)
+    same_bits(ff.dot2(x, y).cpu().numpy(), replay.reduce_replay(terms, gr, h, v, pol))
+    gr, h, v = _shape(x, None)
+    terms = np.stack([xn, np.zeros_like(xn)], 1)
+    same_bits(ff.sum2(x).cpu().numpy(), replay.reduce_replay(terms, gr, h, v, pol))
+
+
+@pytest.mark.parametrize("cond", [1e3, 1e6, 1e9, 1e12])
+def test_dot2_ill_conditioned_within_bound(cond):
+    import paper_cs_0603115_gb300 as ff
+    n = 1 << 22
+    g = inputs.ill_dot_f32(n, cond, inputs.seed_for(5, int(math.log10(cond))))
+    x, y = g.x.to(DEV), g.y.to(DEV)
+    r = ff.dot2(x, y).cpu().numpy()
+    _, _, A, E = oracle.exact_dot_f32(g.x.numpy(), g.y.numpy(), r)
+    grid, _, _ = _shape(x, y)
+    u = 2.0 ** -24
+    # s-additions along one path: the thread's own values, then the warp,
+    # block and last-block trees; each adds at most u |p| of error terms
+    m = -(-n // (grid * 256)) + 4 + 5 + 3 + (-(-grid // 256)) + 5 + 3
+    gam = m * u / (1 - m * u)
+    assert abs(E) <= gam * u * (m + 1) * A
+    # and in practice at the level of u^2
+    assert abs(E) <= 2.0 ** -40 * A

@@ -495,3 +495,101 @@ def test_fp32_baselines(orc):
     np.testing.assert_array_equal(orc.fp32_add(a, b), a + b)
     np.testing.assert_array_equal(orc.fp32_mul(a, b), a * b)
     np.testing.assert_array_equal(orc.fp32_mad(a, b, c), (a * b) + c)
+
+
+# --------------------------------------------------------------------------
+# accurate addition (Joldes-Muller-Popescu Algorithm 6): no cancellation term
+# --------------------------------------------------------------------------
+U24 = 2.0 ** -24
+ACC_ADD_BOUND = 3 * U24 * U24 / (1 - 4 * U24)
+
+
+def test_add22_accurate_bound_random_with_cancellation(orc):
+    a, b, _ = rand_ff(1 << 17, inputs.seed_for(0, 14), cancel=0.3)
+    r = orc.add22_accurate(a, b)
+    re = orc.relerr("add", a, b, r)
+    assert re.max() <= ACC_ADD_BOUND
+    # the paper's Add22 exceeds it by orders of magnitude on the same inputs
+    assert orc.relerr("add", a, b, orc.add22(a, b)).max() > 2.0 ** -30
+
+
+def test_add22_accurate_bruteforce(orc):
+    F = ff_subset()
+    idx = np.random.default_rng(9).choice(F.shape[0], size=(400000, 2))
+    a, b = F[idx[:, 0]], F[idx[:, 1]]
+    assert orc.relerr("add", a, b, orc.add22_accurate(a, b)).max() <= ACC_ADD_BOUND
+
+
+def test_add22_accurate_special_cases(orc):
+    ab = all_pairs(subset_floats()[::2])
+    z = np.zeros(len(ab), np.float32)
+    r = orc.add22_accurate(np.stack([ab[:, 0], z], 1), np.stack([ab[:, 1], z], 1))
+    assert np.all(r == orc.add12(ab))
+    r = orc.add22_accurate(ff(1.0, 2.0 ** -30), ff(-1.0, 2.0 ** -31))
+    assert r[0, 0] == f32(1.5 * 2.0 ** -30) and r[0, 1] == 0
+    # cancellation that Add22 gets wrong: (1, 2^-25) + (-(1 - 2^-24), -2^-48)
+    a, b = ff(1.0, 2.0 ** -25), ff(-(1 - 2.0 ** -24), -(2.0 ** -48))
+    r = orc.add22_accurate(a, b)
+    want = Fraction(1) + Fraction(1, 2 ** 25) - (1 - Fraction(1, 2 ** 24)) - Fraction(1, 2 ** 48)
+    got = Fraction(float(r[0, 0])) + Fraction(float(r[0, 1]))
+    assert abs(got - want) <= abs(want) * Fraction(ACC_ADD_BOUND)
+
+
+# --------------------------------------------------------------------------
+# Sum2 / Dot2 (Ogita-Rump-Oishi) on binary32 vectors
+# --------------------------------------------------------------------------
+
+def gamma(n):
+    return n * U24 / (1 - n * U24)
+
+
+@pytest.mark.parametrize("cond", [1e3, 1e8, 1e12])
+def test_dot2_within_oro_bound_small_n(orc, cond):
+    # n small enough that gamma_n^2 << u: a dropped error term would show
+    for seed in range(20):
+        g = inputs.ill_dot_f32(32, cond, inputs.seed_for(5, seed))
+        x, y = g.x.numpy(), g.y.numpy()
+        r = orc.dot2(x, y)
+        _, _, A, E = orc.exact_dot_f32(x, y, r)
+        assert abs(E) <= gamma(32) ** 2 * A
+
+
+def test_sum2_within_oro_bound_and_exact_cases(orc):
+    rng = np.random.default_rng(10)
+    for _ in range(20):
+        x = (rng.standard_normal(48) * 2.0 ** rng.integers(-20, 20, 48)).astype(np.float32)
+        x = np.concatenate([x, -x[:24] * np.float32(1 + 2.0 ** -20)])
+        r = orc.sum2(x)
+        _, _, A, E = orc.exact_dot_f32(x, None, r)
+        assert abs(E) <= gamma(len(x)) ** 2 * A
+    # sums that fit a float-float exactly come out exact
+    x = np.array([1.0, 2.0 ** -30, -1.0, 2.0 ** -40, 3.0], np.float32)
+    r = orc.sum2(x)
+    assert Fraction(float(r[0])) + Fraction(float(r[1])) == sum(Fraction(float(v)) for v in x)
+
+
+def test_dot2_reduces_to_sum2_and_twoproduct(orc):
+    rng = np.random.default_rng(11)
+    x = (rng.standard_normal(1000) * 2.0 ** rng.integers(-10, 10, 1000)).astype(np.float32)
+    one = np.ones_like(x)
+    assert np.all(orc.dot2(x, one) == orc.sum2(x))
+    r = orc.dot2(x[:1], x[1:2])
+    assert np.all(r == orc.mul12(np.array([[x[0], x[1]]], np.float32))[0])
+
+
+def test_gemv_dA_outer_product_and_bound(orc):
+    m, n = 12, 17
+    gi = inputs.gemv(m, n, 1, inputs.seed_for(4, 40))
+    dY, X = gi.dY.numpy(), gi.X.numpy()
+    dA = orc.gemv_dA(dY, X)
+    # k = 1: every element is one Mul22 (Add22 with (0, 0) returns it)
+    want = orc.mul22(np.repeat(dY[0], n, axis=0), np.tile(X[0], (m, 1))).reshape(m, n, 2)
+    np.testing.assert_array_equal(dA, want)
+    k = 9
+    gi = inputs.gemv(m, n, k, inputs.seed_for(4, 41))
+    dY, X = gi.dY.numpy(), gi.X.numpy()
+    dA = orc.gemv_dA(dY, X)
+    for r in range(m):
+        for j in range(n):
+            _, _, Aabs, E = orc.exact_dot(np.ascontiguousarray(dY[:, r]), np.ascontiguousarray(X[:, j]), dA[r, j])
+            assert abs(E) <= k * 2.0 ** -44 * Aabs

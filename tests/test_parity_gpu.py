@@ -295,3 +295,20 @@ def test_full_size_sampled_bitexact():
     assert e.b[:, 0].abs().min().item() >= 2.0 ** -60
     del out, e
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("m,n,k", [(33, 64, 1), (17, 129, 5), (64, 256, 64)])
+def test_gemv_dA_bitexact(m, n, k):
+    gi = inputs.gemv(m, n, k, inputs.seed_for(4, 50 + k))
+    dA = ff.gemv_dA(gpu(gi.dY), gpu(gi.X)).cpu().numpy()
+    same_bits(dA, oracle.gemv_dA(gi.dY.numpy(), gi.X.numpy()))
+
+
+def test_gemv_autograd_weight_gradient():
+    gi = inputs.gemv(48, 80, 3, inputs.seed_for(4, 60))
+    A = gpu(gi.A).requires_grad_(True)
+    X = gpu(gi.X).requires_grad_(True)
+    Y = ff.ffgemv(A, X)
+    Y.backward(gpu(gi.dY))
+    same_bits(A.grad.cpu().numpy(), oracle.gemv_dA(gi.dY.numpy(), gi.X.numpy()))
+    same_bits(X.grad.cpu().numpy(), ff.gemv_t(gpu(gi.A), gpu(gi.dY)).cpu().numpy())
