@@ -25,59 +25,87 @@ CFLAGS = ["-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math",
           "-fno-unsafe-math-optimizations", "-fPIC", "-shared"]
 
 
+def compile_sources(sources, out_path: str) -> str:
+    """Compile the given C sources into a shared library with the oracle's
+    flags."""
+    tmp = out_path + f".tmp{os.getpid()}"
+    subprocess.run(["gcc", *CFLAGS, "-o", tmp, *sources, "-lm"], check=True)
+    os.replace(tmp, out_path)
+    return out_path
+
+
 def build(force: bool = False) -> str:
     """Compile liboracle.so with gcc (no contraction, no fast-math)."""
     newest = max(os.path.getmtime(s) for s in SOURCES)
     if (not force and os.path.exists(LIB_PATH)
             and os.path.getmtime(LIB_PATH) >= newest):
         return LIB_PATH
-    tmp = LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["gcc", *CFLAGS, "-o", tmp, *SOURCES, "-lm"]
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB_PATH)
-    return LIB_PATH
+    return compile_sources(SOURCES, LIB_PATH)
 
 
 _lib = None
+
+
+def _bind(path: str) -> ctypes.CDLL:
+    L = ctypes.CDLL(path)
+    _declare(L)
+    return L
+
+
+def swap_library(path):
+    """Bind the wrappers to another build of the oracle sources (a library
+    at `path`, or the default build when path is None); returns the previous
+    binding's path.  Used by the tests that plant a mistake in a copy of the
+    oracle and check that the pins catch it."""
+    global _lib, _lib_path
+    prev = _lib_path
+    _lib = _bind(path) if path else None
+    _lib_path = path
+    return prev
+
+
+_lib_path = None
 
 
 def lib() -> ctypes.CDLL:
     global _lib
     if _lib is None:
         build()
-        L = ctypes.CDLL(LIB_PATH)
-        P, S, I64, D = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int64, ctypes.c_double
-        sig = {
-            "orc_add12": [P, P, S], "orc_split": [P, P, S],
-            "orc_mul12_dekker": [P, P, S], "orc_mul12": [P, P, S],
-            "orc_add22": [P, P, P, S], "orc_mul22": [P, P, P, S],
-            "orc_mul22_dekker": [P, P, P, S], "orc_div22": [P, P, P, S],
-            "orc_add22_accurate": [P, P, P, S], "orc_sum2": [P, S, P], "orc_dot2": [P, P, S, P],
-            "exact_dot_f32": [P, P, S, P, P],
-            "orc_sqrt22": [P, P, S], "orc_sum": [P, S, P],
-            "orc_dot": [P, P, S, P], "orc_dot_backward": [P, P, P, P, P, S],
-            "orc_axpy": [P, P, P, P, S],
-            "orc_gemv": [P, I64, I64, I64, P, I64, I64, P, I64],
-            "orc_gemv_t": [P, I64, I64, I64, P, I64, I64, P, I64],
-            "orc_gemv_dA": [P, I64, I64, P, I64, I64, I64, P, I64],
-            "orc_fp32_add": [P, P, P, S], "orc_fp32_mul": [P, P, P, S],
-            "orc_fp32_mad": [P, P, P, P, S],
-            "exact_sum_f64_q": [P, S, P], "exact_count_sum2_mismatch": [P, P, S],
-            "exact_count_prod_mismatch": [P, P, S], "exact_add22_bound": [P, P, P, P, S],
-            "exact_relerr_ff": [ctypes.c_int, P, P, P, P, S], "exact_dot_ff": [P, P, S, P, P],
-        }
-        for name, args in sig.items():
-            fn = getattr(L, name)
-            fn.argtypes = args
-            fn.restype = None
-        L.exact_count_sum2_mismatch.restype = S
-        L.exact_count_prod_mismatch.restype = S
-        L.exact_sum_f64.argtypes = [P, S]
-        L.exact_sum_f64.restype = D
-        L.orc_canary_mul_add.argtypes = [ctypes.c_float] * 3
-        L.orc_canary_mul_add.restype = ctypes.c_float
-        _lib = L
+        _lib = _bind(LIB_PATH)
     return _lib
+
+
+def _declare(L: ctypes.CDLL) -> None:
+    P, S, I64, D = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int64, ctypes.c_double
+    sig = {
+        "orc_add12": [P, P, S], "orc_split": [P, P, S],
+        "orc_mul12_dekker": [P, P, S], "orc_mul12": [P, P, S],
+        "orc_add22": [P, P, P, S], "orc_mul22": [P, P, P, S],
+        "orc_mul22_dekker": [P, P, P, S], "orc_div22": [P, P, P, S],
+        "orc_add22_accurate": [P, P, P, S], "orc_sum2": [P, S, P], "orc_dot2": [P, P, S, P],
+        "exact_dot_f32": [P, P, S, P, P],
+        "orc_sqrt22": [P, P, S], "orc_sum": [P, S, P],
+        "orc_dot": [P, P, S, P], "orc_dot_backward": [P, P, P, P, P, S],
+        "orc_axpy": [P, P, P, P, S],
+        "orc_gemv": [P, I64, I64, I64, P, I64, I64, P, I64],
+        "orc_gemv_t": [P, I64, I64, I64, P, I64, I64, P, I64],
+        "orc_gemv_dA": [P, I64, I64, P, I64, I64, I64, P, I64],
+        "orc_fp32_add": [P, P, P, S], "orc_fp32_mul": [P, P, P, S],
+        "orc_fp32_mad": [P, P, P, P, S],
+        "exact_sum_f64_q": [P, S, P], "exact_count_sum2_mismatch": [P, P, S],
+        "exact_count_prod_mismatch": [P, P, S], "exact_add22_bound": [P, P, P, P, S],
+        "exact_relerr_ff": [ctypes.c_int, P, P, P, P, S], "exact_dot_ff": [P, P, S, P, P],
+    }
+    for name, args in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = None
+    L.exact_count_sum2_mismatch.restype = S
+    L.exact_count_prod_mismatch.restype = S
+    L.exact_sum_f64.argtypes = [P, S]
+    L.exact_sum_f64.restype = D
+    L.orc_canary_mul_add.argtypes = [ctypes.c_float] * 3
+    L.orc_canary_mul_add.restype = ctypes.c_float
 
 
 def _f32(a) -> np.ndarray:
