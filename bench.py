@@ -669,7 +669,13 @@ def run_case(args):
     else:
         e = inputs.elementwise(n, inputs.seed_for(1, 0), device=dev)
         outs = [torch.empty_like(e.a) for _ in OPS]
-        fn = make_step(ff, e, outs)[args.case]
+        step = make_step(ff, e, outs)
+        if args.case == "step":
+            def fn():
+                for op in OPS:
+                    step[op]()
+        else:
+            fn = step[args.case]
     torch.cuda.synchronize()
     for _ in range(args.reps):
         fn()
@@ -681,8 +687,9 @@ def paper_table(args):
     """The paper's timing method (Section 6, Tables 3 and 4) regenerated:
     times of FP32 add / mul / mad, Add12, Mul12, Add22 and Mul22 over 4096 ..
     1048576 values, normalised to the time of 4096 FP32 additions on the same
-    device -- on the GB300 (CUDA events, mean of 50 launches after warm-up)
-    and on one host core (the oracle's loops, the CPU-baseline leg)."""
+    device -- on the GB300 (device time per launch: 50 launches replayed from
+    one CUDA graph) and on one host core (the oracle's loops, the
+    CPU-baseline leg; best of 20)."""
     import torch
     import paper_cs_0603115_gb300 as ff
     from paper_cs_0603115_gb300 import build as ffbuild
@@ -700,7 +707,7 @@ def paper_table(args):
         fns = [lambda: ff.f32_add(a32, b32, out=o32), lambda: ff.f32_mul(a32, b32, out=o32),
                lambda: ff.f32_mad(a32, b32, c32, out=o32), lambda: ff.add12(e.ab, out=o),
                lambda: ff.mul12(e.ab, out=o), lambda: ff.add(e.a, e.b, out=o), lambda: ff.mul(e.a, e.b, out=o)]
-        gpu_t[n] = [time_fn(torch, f, 50, warm=5) for f in fns]
+        gpu_t[n] = [graph_time(torch, f, 50) for f in fns]
         cpu_t[n] = cpu_paper_row(e)
     base_g, base_c = gpu_t[4096][0], cpu_t[4096][0]
     lines = ["| size | " + " | ".join(cols) + " |", "|---" * (len(cols) + 1) + "|"]
@@ -713,6 +720,21 @@ def paper_table(args):
             lines.append(f"| {n} | " + " | ".join(f"{v:.2f}" for v in norm) + " |")
     print("\n".join(lines))
     print(json.dumps(out))
+
+
+def graph_time(torch, fn, reps: int) -> float:
+    """Device time per launch: `reps` launches captured in one CUDA graph and
+    replayed, so the host's launch overhead does not count."""
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        fn()
+    torch.cuda.current_stream().wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        for _ in range(reps):
+            fn()
+    return time_fn(torch, g.replay, 5, warm=2) / reps
 
 
 def cpu_paper_row(e):

@@ -102,11 +102,25 @@ template <> struct V16<float2> { using V = float4; static constexpr int E = 2; }
 template <> struct V16<double> { using V = double2; static constexpr int E = 2; };
 template <> struct V16<float> { using V = float4; static constexpr int E = 4; };
 
-template <typename T>
-union Pack2 {
-    typename V16<T>::V v;
-    T e[V16<T>::E];
-};
+// Explicit split of a 16-byte vector into its values (see ff_stream.cuh on
+// why not a union).
+__device__ __forceinline__ void split_vec(const float4& v, float2 (&e)[2])
+{
+    e[0] = make_float2(v.x, v.y);
+    e[1] = make_float2(v.z, v.w);
+}
+__device__ __forceinline__ void split_vec(const double2& v, double (&e)[2])
+{
+    e[0] = v.x;
+    e[1] = v.y;
+}
+__device__ __forceinline__ void split_vec(const float4& v, float (&e)[4])
+{
+    e[0] = v.x;
+    e[1] = v.y;
+    e[2] = v.z;
+    e[3] = v.w;
+}
 
 // Steps 2-3: the block's combined value ends in thread 0.
 template <class P>
@@ -152,23 +166,30 @@ reduce_kernel(const typename P::T* x, const typename P::T* y, size_t n, int head
     const V* yv = reinterpret_cast<const V*>((P::kDot ? y : x) + h);
     size_t i = tid;
     for (; i + (U - 1) * nthr < nv; i += U * nthr) {
-        Pack2<T> xs[U], ys[U];
+        V xs[U], ys[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            xs[u].v = __ldcs(xv + i + u * nthr);
-            if (P::kDot) ys[u].v = __ldcs(yv + i + u * nthr);
+            xs[u] = __ldcs(xv + i + u * nthr);
+            if (P::kDot) ys[u] = __ldcs(yv + i + u * nthr);
         }
 #pragma unroll
-        for (int u = 0; u < U; ++u)
+        for (int u = 0; u < U; ++u) {
+            T xe[E], ye[E];
+            split_vec(xs[u], xe);
+            if (P::kDot) split_vec(ys[u], ye);
 #pragma unroll
-            for (int e = 0; e < E; ++e) acc = P::step(acc, xs[u].e[e], P::kDot ? ys[u].e[e] : T());
+            for (int e = 0; e < E; ++e) acc = P::step(acc, xe[e], P::kDot ? ye[e] : T());
+        }
     }
     for (; i < nv; i += nthr) {
-        Pack2<T> xs, ys;
-        xs.v = __ldcs(xv + i);
-        if (P::kDot) ys.v = __ldcs(yv + i);
+        V xs, ys;
+        xs = __ldcs(xv + i);
+        if (P::kDot) ys = __ldcs(yv + i);
+        T xe[E], ye[E];
+        split_vec(xs, xe);
+        if (P::kDot) split_vec(ys, ye);
 #pragma unroll
-        for (int e = 0; e < E; ++e) acc = P::step(acc, xs.e[e], P::kDot ? ys.e[e] : T());
+        for (int e = 0; e < E; ++e) acc = P::step(acc, xe[e], P::kDot ? ye[e] : T());
     }
     if (tid == 0)
         for (size_t j = h + nv * E; j < n; ++j) acc = P::step(acc, x[j], P::kDot ? y[j] : T());
