@@ -8,11 +8,11 @@
 // issues U vector loads per input before computing.
 //
 // Residency: a GB300 sustains the highest read+write DRAM throughput on these
-// kernels with about 40-50 KB of loads in flight per SM, not with every SM
-// full: measured on 2^28 values, Add22 reaches ~7.0 TB/s with U = 2 and 3
-// blocks of 256 per SM against ~6.6 TB/s at full occupancy, and the
-// one-input kernels ~6.6 TB/s with U = 2 and 5 blocks per SM.  The launcher
-// therefore caps the grid at SMs x kBlocksPerSm[NIN].
+// kernels with a moderate number of loads in flight per SM, not with every
+// SM full: measured on 2^28 values with the pipelined sweep below (U = 2),
+// the two-input operators reach ~7.0 TB/s with 3 blocks of 256 per SM
+// against ~6.6 TB/s at full occupancy, the one-input operators ~6.8 TB/s
+// with 4.  The launcher caps the grid at SMs x blocks_per_sm(NIN).
 //
 // Alignment: device arrays are only required to be aligned to sizeof(T).
 // If all arrays share the same offset modulo 16 bytes, a scalar head of
@@ -106,7 +106,11 @@ __device__ __forceinline__ void apply_vec(const Op& op, const typename Vec<T>::V
 }
 
 // Vector path: elements [0, head) and the tail are scalar; the body is
-// processed as 16-byte vectors, U per input per thread per sweep.
+// processed as 16-byte vectors, U per input per thread per sweep.  The sweep
+// is software-pipelined: the loads of sweep s + 1 are issued before the
+// values of sweep s are computed and stored, so each thread keeps loads in
+// flight while it computes.  (The scalar head and tail come after the sweep:
+// placed before it, they made the compiler schedule the Add22 loop worse.)
 template <typename T, int NIN, int NOUT, class Op, int U>
 __global__ void __launch_bounds__(kBlock) stream_vec(Args<T, NIN, NOUT> a, Op op)
 {
@@ -118,9 +122,6 @@ __global__ void __launch_bounds__(kBlock) stream_vec(Args<T, NIN, NOUT> a, Op op
     const size_t nv = (a.n - head) / E;            // full vectors
     const size_t tail0 = head + nv * E;            // first tail element
 
-    if (tid < head) scalar_at(a, op, tid);
-    if (tid < a.n - tail0) scalar_at(a, op, tail0 + tid);
-
     const V* in[NIN];
     V* out[NOUT];
 #pragma unroll
@@ -129,14 +130,32 @@ __global__ void __launch_bounds__(kBlock) stream_vec(Args<T, NIN, NOUT> a, Op op
     for (int k = 0; k < NOUT; ++k) out[k] = reinterpret_cast<V*>(a.out[k] + head);
 
     size_t i = tid;
-    for (; i + (U - 1) * nthr < nv; i += U * nthr) {
-        V x[U][NIN];
+    bool full = i + (U - 1) * nthr < nv;
+    V cur[U][NIN];
+    if (full) {
 #pragma unroll
         for (int u = 0; u < U; ++u)
 #pragma unroll
-            for (int k = 0; k < NIN; ++k) x[u][k] = __ldcs(in[k] + i + u * nthr);
+            for (int k = 0; k < NIN; ++k) cur[u][k] = __ldcs(in[k] + i + u * nthr);
+    }
+    while (full) {
+        const size_t nx = i + U * nthr;
+        const bool nfull = nx + (U - 1) * nthr < nv;
+        V nxt[U][NIN];
+        if (nfull) {
 #pragma unroll
-        for (int u = 0; u < U; ++u) apply_vec<T, NIN, NOUT>(op, x[u], out, i + u * nthr);
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int k = 0; k < NIN; ++k) nxt[u][k] = __ldcs(in[k] + nx + u * nthr);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) apply_vec<T, NIN, NOUT>(op, cur[u], out, i + u * nthr);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int k = 0; k < NIN; ++k) cur[u][k] = nxt[u][k];
+        i = nx;
+        full = nfull;
     }
     for (; i < nv; i += nthr) {
         V x[NIN];
@@ -144,6 +163,9 @@ __global__ void __launch_bounds__(kBlock) stream_vec(Args<T, NIN, NOUT> a, Op op
         for (int k = 0; k < NIN; ++k) x[k] = __ldcs(in[k] + i);
         apply_vec<T, NIN, NOUT>(op, x, out, i);
     }
+
+    if (tid < head) scalar_at(a, op, tid);
+    if (tid < a.n - tail0) scalar_at(a, op, tail0 + tid);
 }
 
 // Scalar path for arrays whose offsets modulo 16 bytes differ.
@@ -171,7 +193,7 @@ __global__ void __launch_bounds__(kBlock) stream_scalar(Args<T, NIN, NOUT> a, Op
 }
 
 // Resident 256-thread blocks per SM by number of input arrays (see above).
-constexpr int blocks_per_sm(int nin) { return nin == 1 ? 5 : nin == 2 ? 3 : 2; }
+constexpr int blocks_per_sm(int nin) { return nin == 1 ? 4 : nin == 2 ? 3 : 2; }
 
 // Host launcher: validates nothing (the caller did), picks the path and the
 // grid, launches on `s`.
