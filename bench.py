@@ -204,17 +204,35 @@ def cpu_baseline(e_gpu, min_seconds: float = 10.0):
                       f"{dt:.1f} s, single-threaded C oracle"}
 
 
-def traffic_for(kernel: str, build_id: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on this exact build (else None)."""
+# sources that define the elementwise kernels (and their flags)
+ELEMENTWISE_SOURCES = ("paper_cs_0603115_gb300/csrc/ff_core.cuh", "paper_cs_0603115_gb300/csrc/ff_stream.cuh",
+                       "paper_cs_0603115_gb300/csrc/ff_elementwise.cu", "paper_cs_0603115_gb300/csrc/ff_host.cuh",
+                       "paper_cs_0603115_gb300/build.py")
+
+
+def kernel_fingerprint(files=ELEMENTWISE_SOURCES) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(f.encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kernel: str, n: int):
+    """DRAM bytes per launch for `kernel` on n values, from the committed ncu
+    summary (profiles/traffic.json), scaled from the captured size in
+    proportion to the values processed; None when the kernel's sources
+    changed since the capture."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
-    ent = d.get(kernel)
-    if not ent or ent.get("build_id") != build_id:
+    ent = d.get("kernels", {}).get(kernel)
+    if not ent or d.get("fingerprint") != kernel_fingerprint():
         return None
-    return ent.get("dram_bytes_per_launch")
+    return ent["dram_bytes_per_launch"] * n / d["n_captured"]
 
 
 def run_gpu(args):
@@ -279,10 +297,12 @@ def run_gpu(args):
     ach = BYTES_PER_VALUE[dom] * n / per_op[dom] / 1e9
     kname = {"add12": "ff_add12", "mul12": "ff_mul12", "add": "ff_add", "mul": "ff_mul", "div": "ff_div",
              "sqrt": "ff_sqrt"}[dom]
-    traffic = traffic_for(kname, build_id)
+    traffic = traffic_for(kname, n)
     roofline = {"bound": "hbm", "achieved": round(ach, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": round(ach / peaks["hbm_gbs"], 4), "traffic": traffic, "kernel": kname,
                 "algorithmic_bytes_per_launch": BYTES_PER_VALUE[dom] * n,
+                "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one 2^26-value launch, "
+                                "scaled x4 to 2^28 (traffic grows in proportion)",
                 "peak_source": peaks["source"] + " copy bandwidth"}
 
     # end to end through host buffers: every step copies its inputs from
@@ -766,12 +786,16 @@ def main():
     p.add_argument("--rows", choices=["all", "main"], default="all")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--fingerprint", action="store_true", help="print the elementwise kernels' source fingerprint")
     p.add_argument("--paper-table", action="store_true", help="regenerate the paper's normalised timing tables")
     p.add_argument("--case", default=None, help="profiling case: one operator on --n values, --reps launches")
     p.add_argument("--n", type=int, default=1 << 24)
     p.add_argument("--k", type=int, default=1)
     p.add_argument("--reps", type=int, default=3)
     args = p.parse_args()
+    if args.fingerprint:
+        print(kernel_fingerprint())
+        return
     if args.case:
         run_case(args)
         return
