@@ -211,12 +211,21 @@ ELEMENTWISE_SOURCES = ("paper_cs_0603115_gb300/csrc/ff_core.cuh", "paper_cs_0603
 
 
 def kernel_fingerprint(files=ELEMENTWISE_SOURCES) -> str:
+    """Hash of the kernels' sources with comments and blank space removed, so
+    that only a change of code makes a stored profile stale."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for f in files:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(f.encode())
-            h.update(fh.read())
+        text = open(os.path.join(ROOT, f)).read()
+        if f.endswith(".py"):
+            text = re.sub(r'"""(.|\n)*?"""', "", text)
+            text = re.sub(r"#[^\n]*", "", text)
+        else:
+            text = re.sub(r"/\*(.|\n)*?\*/", "", text)
+            text = re.sub(r"//[^\n]*", "", text)
+        h.update(f.encode())
+        h.update(re.sub(r"\s+", " ", text).strip().encode())
     return h.hexdigest()[:16]
 
 

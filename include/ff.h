@@ -3,9 +3,9 @@
  *
  * Float-float arithmetic after Da Graca & Defour, "Implementation of
  * float-float operators on graphics hardware" (arXiv cs/0603115): a number is
- * the unevaluated sum hi + lo of two IEEE binary32 values (Section 4,
- * "Proposed format"), about 44 bits of precision with the exponent range of
- * binary32 (Section 7).
+ * the unevaluated sum hi + lo of two IEEE binary32 values (the format of
+ * Section 4), about 44 bits of precision with the exponent range of binary32
+ * (Section 7).
  *
  * Conventions that hold for every entry point unless its comment says
  * otherwise:
@@ -117,7 +117,7 @@ FF_API ff_status ff_sqrt(const ff2* a, ff2* out, size_t n, cudaStream_t s);
 FF_API ff_status ff_axpy(ff2 alpha, const ff2* x, const ff2* y, ff2* z, size_t n, cudaStream_t s);
 
 /* ------------------------------------------------------------------------ */
-/* Compensated reductions (Section 7's "compensated algorithms")             */
+/* Compensated reductions (future work of Section 7)                       */
 /* ------------------------------------------------------------------------ */
 
 /* Workspace bytes for ff_sum / ff_dot / ff_f64_dot on the current device
@@ -180,7 +180,7 @@ FF_API ff_status ff_dot_backward(const ff2* dout_dev, const ff2* x, const ff2* y
                           size_t n, cudaStream_t s);
 
 /* Compensated sum and dot product of plain binary32 vectors (the paper's
- * "compensated algorithms", Section 7): Ogita, Rump and Oishi's Sum2 and
+ * compensated algorithms, future work in Section 7): Ogita, Rump and Oishi's Sum2 and
  * Dot2 (2005) with Add12 as TwoSum and the fused Mul12 as TwoProduct, per
  * thread in the sweep order of ff_sum, combined across threads, warps and
  * blocks by (p, q) = TwoSum(a.p, b.p), s = a.s + (b.s + q).  *out_dev is the

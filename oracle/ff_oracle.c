@@ -35,7 +35,8 @@
  *     paper's Add12 as the final renormalisation.
  *   - Reductions (sum, dot), AXPY, GEMV and the dot backward are not in the
  *     paper either; they are the plain left-to-right Add22 accumulation of
- *     the paper's operators ("compensated algorithms", Section 7).
+ *     the paper's operators (the compensated algorithms Section 7 names as
+ *     future work).
  */
 #include <math.h>
 #include <stddef.h>
@@ -374,7 +375,8 @@ void orc_add22_accurate(const float *a, const float *b, float *r, size_t n)
 }
 
 /* Compensated summation and dot product of binary32 vectors (the
- * "compensated algorithms" of Section 7): Ogita, Rump and Oishi, "Accurate
+ * compensated algorithms Section 7 names as future work): Ogita, Rump and
+ * Oishi, "Accurate
  * sum and dot product" (SIAM J. Sci. Comput. 2005), Sum2 and Dot2, in their
  * left-to-right order, with the paper's Add12 as TwoSum and the fused Mul12
  * as TwoProduct.  The result is returned unrounded as the float-float value

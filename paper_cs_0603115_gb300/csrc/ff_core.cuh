@@ -5,7 +5,7 @@
 // only fused multiply-add is the explicit one of Mul12.
 //
 // A float-float value is a float2 {x = hi, y = lo}: the unevaluated sum
-// hi + lo (Section 4, "Proposed format").
+// hi + lo (the format of Section 4).
 #pragma once
 #include <cuda_runtime.h>
 

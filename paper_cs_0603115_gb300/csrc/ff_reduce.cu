@@ -1,6 +1,7 @@
 // ff_reduce.cu -- deterministic compensated reductions: the float-float sum
 // and dot product (Add22 accumulation of the paper's operators, the
-// "compensated algorithms" of Section 7) and a binary64 dot baseline.
+// compensated algorithms Section 7 names as future work) and a binary64 dot
+// baseline.
 //
 // One launch per reduction.  Order of combination (fixed for a given n,
 // device and build, hence bit-reproducible):

@@ -3,8 +3,8 @@
 This module holds no float-float arithmetic: it only draws random binary64
 values and stores each as a float-float pair (hi, lo) = (RN32(d), RN32(d - hi)),
 the format of Section 4 of the paper (an unevaluated sum of two binary32
-numbers).  The paper evaluates its operators on "randomly generated test
-vectors" (Section 6.1); the recipes below are the synthetic stand-ins.
+numbers).  The paper measured its operators on random inputs (Section 6.1);
+the recipes below are the synthetic stand-ins.
 
 Every generator takes a seed and a torch device.  The same seed on the same
 device and torch version gives the same arrays; the CPU oracle and the CUDA
