@@ -312,3 +312,46 @@ def test_gemv_autograd_weight_gradient():
     Y.backward(gpu(gi.dY))
     same_bits(A.grad.cpu().numpy(), oracle.gemv_dA(gi.dY.numpy(), gi.X.numpy()))
     same_bits(X.grad.cpu().numpy(), ff.gemv_t(gpu(gi.A), gpu(gi.dY)).cpu().numpy())
+
+
+# ---------------------------------------------------------------------------
+# maximum sizes: more than 2^32 values (64-bit indexing end to end)
+# ---------------------------------------------------------------------------
+
+def _big_pattern(n, scale, dev):
+    """Cheap deterministic float-float values for very large n: hi = 1 + (i
+    mod 4093) 2^-12 times `scale`, lo = hi 2^-30 (i mod 7 - 3) / 4 (exact)."""
+    i = torch.arange(n, device=dev, dtype=torch.int64)
+    hi = (1.0 + (i % 4093).to(torch.float32) * 2.0 ** -12) * scale
+    lo = hi * ((i % 7 - 3).to(torch.float32) * 2.0 ** -32)
+    del i
+    return torch.stack([hi, lo], dim=1)
+
+
+def test_more_than_2_32_values_elementwise_and_dot():
+    free, _ = torch.cuda.mem_get_info()
+    n = (1 << 32) + 5
+    if free < (180 << 30):
+        pytest.skip("needs ~180 GB of free device memory (three 32 GiB arrays and temporaries)")
+    a = _big_pattern(n, 1.0, DEV)
+    b = _big_pattern(n, -0.75, DEV)
+    out = ff.add(a, b)
+    idx = torch.cat([torch.arange(8), torch.randint(0, n, (1 << 16,), generator=torch.Generator().manual_seed(5)),
+                     torch.arange((1 << 32) - 4, n)]).to(DEV)
+    an, bn = a[idx].cpu().numpy(), b[idx].cpu().numpy()
+    same_bits(out[idx].cpu().numpy(), oracle.add22(an, bn))
+    ff.mul(a, b, out=out)
+    same_bits(out[idx].cpu().numpy(), oracle.mul22(an, bn))
+    del out, b
+    torch.cuda.empty_cache()
+    # sum of n ones: every partial sum is an integer below 2^48, exact in
+    # float-float, so the result is exactly (RN32(n), n - RN32(n))
+    a.zero_()
+    a[:, 0] = 1.0
+    r = ff.sum(a).cpu().numpy()
+    hi = np.float32(n)
+    assert r[0] == hi and float(r[1]) == float(n - float(hi))
+    r = ff.dot(a, a).cpu().numpy()
+    assert r[0] == hi and float(r[1]) == float(n - float(hi))
+    del a
+    torch.cuda.empty_cache()
