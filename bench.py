@@ -634,7 +634,73 @@ def batched_rows(torch, ff, inputs, dev, peaks):
     pb.close()
     del X, Y, Z, W, D, Dplain, dout
     torch.cuda.empty_cache()
+    rows.update(batched_gemv_row(torch, ff, inputs, dev, hbm))
     return rows
+
+
+def batched_gemv_row(torch, ff, inputs, dev, hbm):
+    """1024 float-float GEMVs y = A x of uneven shapes (m, n log-uniform over
+    32..4096) in one persistent launch, against 1024 plain ff_gemv calls."""
+    from paper_cs_0603115_gb300 import batch
+    g = torch.Generator().manual_seed(inputs.seed_for(3, 9))
+    cnt = 1024
+    ms = torch.round(2.0 ** (5 + 7 * torch.rand(cnt, generator=g, dtype=torch.float64))).to(torch.int64).tolist()
+    ns = torch.round(2.0 ** (5 + 7 * torch.rand(cnt, generator=g, dtype=torch.float64))).to(torch.int64).tolist()
+    ns = [n + (n & 1) for n in ns]
+    total = sum(m * n for m, n in zip(ms, ns))
+    gA = torch.Generator(device=dev).manual_seed(inputs.seed_for(3, 10))
+    Aall = inputs.to_ff(inputs.loguniform_f64(total, gA, dev))
+    xall = inputs.to_ff(inputs.loguniform_f64(sum(ns), gA, dev))
+    yall = torch.empty((sum(ms), 2), dtype=torch.float32, device=dev)
+    yplain = torch.empty_like(yall)
+    specs, views = [], []
+    oa = ox = oy = 0
+    for m, n in zip(ms, ns):
+        A = Aall[oa:oa + m * n].view(m, n, 2)
+        x = xall[ox:ox + n]
+        y = yall[oy:oy + m]
+        specs.append((batch.GEMV, A, x, y, None))
+        views.append((A, x.view(1, n, 2), yplain[oy:oy + m].view(1, m, 2)))
+        oa += m * n
+        ox += n
+        oy += m
+    inst = batch.make_instances(specs)
+    tune, _ = batch.autotune(inst, reps=2, cache_path=None)
+    plan = batch.BatchPlan(inst, tune=tune).capture()
+
+    def plain():
+        for A, x, y in views:
+            ff.gemv(A, x, out=y)
+
+    t_plain = time_fn(torch, plain, 3, warm=1)
+    gr = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        plain()
+    torch.cuda.current_stream().wait_stream(s)
+    with torch.cuda.graph(gr):
+        plain()
+    t_plain_graph = time_fn(torch, gr.replay, 3, warm=1)
+    t_b = time_fn(torch, plan.launch, 5)
+    # rows agree with the plain GEMV, relative to sum_j |A_rj x_j|
+    rel = 0.0
+    oy = 0
+    for (A, x, yp), (m, n) in zip(views, zip(ms, ns)):
+        den = inputs.ff_to_f64(A).abs() @ inputs.ff_to_f64(x[0]).abs()
+        d = (inputs.ff_to_f64(yall[oy:oy + m]) - inputs.ff_to_f64(yp[0])).abs()
+        rel = max(rel, float((d / den).max()))
+        oy += m
+    plan.close()
+    del Aall, xall, yall, yplain
+    torch.cuda.empty_cache()
+    nbytes = 8 * total
+    return {"batched_1024_gemv": {
+        "A_values": total, "plain_loop_ms": round(t_plain * 1e3, 3), "plain_graph_ms": round(t_plain_graph * 1e3, 3),
+        "batched_graph_ms": round(t_b * 1e3, 3), "speedup_vs_plain_loop": round(t_plain / t_b, 3),
+        "speedup_vs_plain_graph": round(t_plain_graph / t_b, 3), "GB/s": round(nbytes / t_b / 1e9, 1),
+        "frac_hbm": round(nbytes / t_b / 1e9 / hbm, 4), "tune": list(tune),
+        "max_diff_vs_plain_over_sum_abs": rel}}
 
 
 # ---------------------------------------------------------------------------

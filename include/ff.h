@@ -229,7 +229,12 @@ FF_API ff_status ff_gemv_dA(const ff2* dY, int64_t m, int64_t lddy, const ff2* X
 /* Batched dot / AXPY: many instances in one persistent launch               */
 /* ------------------------------------------------------------------------ */
 
-typedef enum ff_batch_kind { FF_BATCH_DOT = 0, FF_BATCH_AXPY = 1, FF_BATCH_DOT_GRAD = 2 } ff_batch_kind;
+typedef enum ff_batch_kind {
+    FF_BATCH_DOT = 0,
+    FF_BATCH_AXPY = 1,
+    FF_BATCH_DOT_GRAD = 2,
+    FF_BATCH_GEMV = 3
+} ff_batch_kind;
 
 /* One instance.
  *   DOT:      *out = sum_i Mul22(x[i], y[i]) (out: one ff2), with the Add22
@@ -239,6 +244,9 @@ typedef enum ff_batch_kind { FF_BATCH_DOT = 0, FF_BATCH_AXPY = 1, FF_BATCH_DOT_G
  *   DOT_GRAD: the adjoint of a dot: out[i] = Mul22(*dout, y[i]) and
  *             out2[i] = Mul22(*dout, x[i]) (dout: one ff2 read on the device
  *             when the run executes), bit-identical to ff_dot_backward.
+ *   GEMV:     out[r] = sum_j Mul22(x[r * lda + j], y[j]) for r < m: x is an
+ *             m x n row-major matrix (row stride lda >= n), y a vector of n
+ *             values, out m values; each row is reduced like a DOT instance.
  * All pointers are device pointers owned by the caller and must stay valid
  * while any plan or graph built from the instance is used; unused pointers
  * may be NULL. */
@@ -252,6 +260,8 @@ typedef struct ff_batch_instance {
     ff2* out2;
     const ff2* dout;
     ff2 alpha;
+    int64_t m;   /* GEMV: rows */
+    int64_t lda; /* GEMV: row stride of x */
 } ff_batch_instance;
 
 /* Launch configuration of the batched kernel: threads per block (128, 256

@@ -23,7 +23,8 @@ class ff2(ctypes.Structure):
 class ff_batch_instance(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("reserved", ctypes.c_int32), ("n", ctypes.c_int64),
                 ("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("out", ctypes.c_void_p),
-                ("out2", ctypes.c_void_p), ("dout", ctypes.c_void_p), ("alpha", ff2)]
+                ("out2", ctypes.c_void_p), ("dout", ctypes.c_void_p), ("alpha", ff2),
+                ("m", ctypes.c_int64), ("lda", ctypes.c_int64)]
 
 
 class ff_tune(ctypes.Structure):

@@ -22,6 +22,7 @@ from ._lib import ff2, ff_batch_instance, ff_tune
 DOT = 0
 AXPY = 1
 DOT_GRAD = 2
+GEMV = 3
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "ff_gb300", "autotune.json")
 
 
@@ -29,7 +30,8 @@ def make_instances(specs) -> ctypes.Array:
     """specs: iterable of (kind, x, y, out, alpha) or (kind, x, y, out, alpha,
     out2, dout) with x, y, out CUDA float-float tensors (out is a (2,) tensor
     for DOT), alpha a (hi, lo) pair (AXPY only), and for DOT_GRAD out = dx,
-    out2 = dy and dout a (2,) device tensor."""
+    out2 = dy and dout a (2,) device tensor.  For GEMV, x is the (m, n, 2)
+    row-major matrix, y the (n, 2) vector and out the (m, 2) result."""
     specs = list(specs)
     arr = (ff_batch_instance * len(specs))()
     for i, spec in enumerate(specs):
@@ -38,7 +40,12 @@ def make_instances(specs) -> ctypes.Array:
         dout = spec[6] if len(spec) > 6 else None
         arr[i].kind = kind
         arr[i].reserved = 0
-        arr[i].n = x.numel() // 2
+        if kind == GEMV:
+            arr[i].n = x.shape[1]
+            arr[i].m = x.shape[0]
+            arr[i].lda = x.shape[1]
+        else:
+            arr[i].n = x.numel() // 2
         arr[i].x = x.data_ptr()
         arr[i].y = y.data_ptr()
         arr[i].out = out.data_ptr()

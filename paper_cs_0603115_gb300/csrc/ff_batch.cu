@@ -12,6 +12,8 @@
 // round robin (block b takes tiles b, b + G, b + 2G, ...).
 //   AXPY tile: z_i = Add22(Mul22(alpha, x_i), y_i) for the tile's values.
 //   dot-gradient tile: dx_i = Mul22(dout, y_i), dy_i = Mul22(dout, x_i).
+//   A GEMV instance becomes one dot record per row (row r of the matrix with
+//   the vector, result to out[r]) when the plan is built.
 //   dot tile:  each thread accumulates its values left to right with
 //              Add22(acc, Mul22(x_i, y_i)); the block combines threads with
 //              the shuffle-down Add22 tree of ff_dot and stores the tile's
@@ -299,9 +301,17 @@ ff_status validate(const ff_batch_instance* inst, int count)
     if (count < 0 || (count > 0 && inst == nullptr)) return FF_ERR_INVALID_ARG;
     for (int i = 0; i < count; ++i) {
         const ff_batch_instance& b = inst[i];
-        if (b.n < 0 || (b.kind != FF_BATCH_DOT && b.kind != FF_BATCH_AXPY && b.kind != FF_BATCH_DOT_GRAD))
+        if (b.n < 0 || (b.kind != FF_BATCH_DOT && b.kind != FF_BATCH_AXPY && b.kind != FF_BATCH_DOT_GRAD &&
+                         b.kind != FF_BATCH_GEMV))
             return FF_ERR_INVALID_ARG;
         const size_t n = static_cast<size_t>(b.n);
+        if (b.kind == FF_BATCH_GEMV) {
+            if (b.m < 0 || b.lda < b.n || b.m > INT32_MAX) return FF_ERR_INVALID_ARG;
+            const size_t m = static_cast<size_t>(b.m);
+            if (!ffh::ok_ptr(b.x, m * static_cast<size_t>(b.lda)) || !ffh::ok_ptr(b.y, n) || !ffh::ok_ptr(b.out, m))
+                return FF_ERR_INVALID_ARG;
+            continue;
+        }
         if (!ffh::ok_ptr(b.x, n) || !ffh::ok_ptr(b.y, n)) return FF_ERR_INVALID_ARG;
         if (b.kind == FF_BATCH_DOT && !ffh::ok_ptr(b.out, 1)) return FF_ERR_INVALID_ARG;
         if (b.kind == FF_BATCH_AXPY && !ffh::ok_ptr(b.out, n)) return FF_ERR_INVALID_ARG;
@@ -331,17 +341,40 @@ ff_status ff_batch_plan_create(const ff_batch_instance* inst, int count, const f
     if (st != FF_OK) return st;
 
     const int64_t tile = static_cast<int64_t>(tune.block) * tune.pairs_per_thread;
-    std::vector<DevInst> hi(static_cast<size_t>(count));
-    std::vector<Tile> ht;
-    int64_t ndot = 0, total = 0;
+    // one record per dot / AXPY / gradient instance and per GEMV row
+    struct Rec {
+        int kind;
+        int64_t n;
+        const void* x;
+        const void* y;
+        void* out;
+        void* out2;
+        const void* dout;
+        ff2 alpha;
+    };
+    std::vector<Rec> recs;
+    recs.reserve(static_cast<size_t>(count));
     for (int i = 0; i < count; ++i) {
         const ff_batch_instance& b = inst[i];
-        DevInst& d = hi[static_cast<size_t>(i)];
-        d.x = reinterpret_cast<const float2*>(b.x);
-        d.y = reinterpret_cast<const float2*>(b.y);
-        d.out = reinterpret_cast<float2*>(b.out);
-        d.out2 = reinterpret_cast<float2*>(b.out2);
-        d.dout = reinterpret_cast<const float2*>(b.dout);
+        if (b.kind == FF_BATCH_GEMV) {
+            for (int64_t r = 0; r < b.m; ++r)
+                recs.push_back(Rec{FF_BATCH_DOT, b.n, b.x + r * b.lda, b.y, b.out + r, nullptr, nullptr, b.alpha});
+        } else {
+            recs.push_back(Rec{b.kind, b.n, b.x, b.y, b.out, b.out2, b.dout, b.alpha});
+        }
+    }
+    if (recs.size() > static_cast<size_t>(INT32_MAX)) return FF_ERR_INVALID_ARG;
+    std::vector<DevInst> hi(recs.size());
+    std::vector<Tile> ht;
+    int64_t ndot = 0, total = 0;
+    for (size_t i = 0; i < recs.size(); ++i) {
+        const Rec& b = recs[i];
+        DevInst& d = hi[i];
+        d.x = static_cast<const float2*>(b.x);
+        d.y = static_cast<const float2*>(b.y);
+        d.out = static_cast<float2*>(b.out);
+        d.out2 = static_cast<float2*>(b.out2);
+        d.dout = static_cast<const float2*>(b.dout);
         d.alpha = make_float2(b.alpha.hi, b.alpha.lo);
         d.n = b.n;
         d.kind = b.kind;
@@ -354,13 +387,13 @@ ff_status ff_batch_plan_create(const ff_batch_instance* inst, int count, const f
         if (nt > INT32_MAX) return FF_ERR_INVALID_ARG;
         d.ntiles = static_cast<int32_t>(nt);
         d.pad = 0;
-        for (int64_t k = 0; k < nt; ++k) ht.push_back(Tile{i, 0, k * tile});
+        for (int64_t k = 0; k < nt; ++k) ht.push_back(Tile{static_cast<int32_t>(i), 0, k * tile});
         ndot += (b.kind == FF_BATCH_DOT);
         total += b.n;
     }
     auto* p = new (std::nothrow) ff_batch_plan();
     if (!p) return FF_ERR_UNSUPPORTED;
-    p->count = count;
+    p->count = static_cast<int>(recs.size());
     p->tune = tune;
     p->ntiles = static_cast<int64_t>(ht.size());
     p->ndot = ndot;
@@ -373,7 +406,7 @@ ff_status ff_batch_plan_create(const ff_batch_instance* inst, int count, const f
     p->grid = static_cast<unsigned>(grid);
     p->d_inst = nullptr;
     p->d_tiles = nullptr;
-    if (count > 0) {
+    if (!hi.empty()) {
         cudaError_t e = cudaMalloc(&p->d_inst, hi.size() * sizeof(DevInst));
         if (e == cudaSuccess && !ht.empty()) e = cudaMalloc(&p->d_tiles, ht.size() * sizeof(Tile));
         if (e == cudaSuccess) e = cudaMemcpy(p->d_inst, hi.data(), hi.size() * sizeof(DevInst), cudaMemcpyHostToDevice);
@@ -497,12 +530,14 @@ size_t ff_batch_autotune_workspace_bytes(const ff_batch_instance* inst, int coun
     // the smallest tile of any candidate gives the most tiles
     int64_t smallest = INT64_MAX;
     for (const Variant& v : kVariants) smallest = std::min<int64_t>(smallest, static_cast<int64_t>(v.block) * v.ppt);
-    size_t ntiles = 0;
+    size_t ntiles = 0, nrec = 0;
     for (int i = 0; i < count; ++i) {
         const int64_t n = inst[i].n;
-        ntiles += static_cast<size_t>(n > 0 ? (n + smallest - 1) / smallest : 1);
+        const size_t reps = inst[i].kind == FF_BATCH_GEMV ? static_cast<size_t>(inst[i].m > 0 ? inst[i].m : 0) : 1;
+        ntiles += reps * static_cast<size_t>(n > 0 ? (n + smallest - 1) / smallest : 1);
+        nrec += reps;
     }
-    const size_t counters = ((static_cast<size_t>(count) * 4 + kCountersAlign - 1) / kCountersAlign) * kCountersAlign;
+    const size_t counters = ((nrec * 4 + kCountersAlign - 1) / kCountersAlign) * kCountersAlign;
     return counters + ntiles * sizeof(float2) + 16;
 }
 

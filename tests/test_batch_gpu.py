@@ -162,3 +162,38 @@ def test_batch_errors():
     plan = batch.BatchPlan(inst)
     assert L.ff_batch_run(plan.handle, plan.ws.data_ptr(), 8, None) == 2   # workspace too small
     plan.close()
+
+
+def test_batch_gemv_instances():
+    """GEMV instances of uneven shapes (rows become dot records) mixed with
+    dots and AXPYs: every row within the dot bound of the exact value, and
+    equal to the plain ff_gemv within twice the bound."""
+    import paper_cs_0603115_gb300 as ff
+    from paper_cs_0603115_gb300 import batch
+    shapes = [(1, 1), (3, 1000), (17, 4097), (64, 9), (0, 5), (5, 0), (40, 20001)]
+    specs, keep = [], []
+    for i, (m, n) in enumerate(shapes):
+        gi = inputs.gemv(m, n, 1, inputs.seed_for(4, 70 + i))
+        A, x = gi.A.to(DEV), gi.X[0].to(DEV).contiguous()
+        out = torch.full((m, 2), float("nan"), dtype=torch.float32, device=DEV)
+        specs.append((batch.GEMV, A, x, out, None))
+        keep.append((gi.A.numpy(), gi.X[0].numpy(), A, x, out))
+    dspecs, dkeep = build_case([100, 7, 4097], [batch.DOT, batch.AXPY, batch.DOT], 8000)
+    plan = batch.BatchPlan(batch.make_instances(specs + dspecs)).capture()
+    plan.launch()
+    torch.cuda.synchronize()
+    check(dkeep)
+    for An, xn, A, x, out in keep:
+        got = out.cpu().numpy()
+        m, n = An.shape[0], An.shape[1]
+        if m and n:
+            plain = ff.gemv(A, x.reshape(1, n, 2))[0].cpu().numpy()
+        for r in range(m):
+            _, _, Aabs, E = oracle.exact_dot(An[r], xn, got[r])
+            assert abs(E) <= max(1, n) * 2.0 ** -46 * Aabs
+            if n:
+                d = abs((float(got[r, 0]) - float(plain[r, 0])) + (float(got[r, 1]) - float(plain[r, 1])))
+                assert d <= 2 * max(1, n) * 2.0 ** -46 * Aabs
+            else:
+                assert got[r, 0] == 0 and got[r, 1] == 0
+    plan.close()
