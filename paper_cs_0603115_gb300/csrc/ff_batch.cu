@@ -12,8 +12,11 @@
 // round robin (block b takes tiles b, b + G, b + 2G, ...).
 //   AXPY tile: z_i = Add22(Mul22(alpha, x_i), y_i) for the tile's values.
 //   dot-gradient tile: dx_i = Mul22(dout, y_i), dy_i = Mul22(dout, x_i).
-//   A GEMV instance becomes one dot record per row (row r of the matrix with
-//   the vector, result to out[r]) when the plan is built.
+//   GEMV rows tile (rows of length <= 65536): warp w of the block reduces
+//   row start + w: lane l accumulates the two-value chunks l, l + 32, ... of
+//   the row with Add22(acc, Mul22(A_rj, x_j)), the warp combines its lanes
+//   with the shuffle-down Add22 tree and lane 0 writes out[r].  Longer GEMV
+//   rows become dot records (row r of the matrix with the vector).
 //   dot tile:  each thread accumulates its values left to right with
 //              Add22(acc, Mul22(x_i, y_i)); the block combines threads with
 //              the shuffle-down Add22 tree of ff_dot and stores the tile's
@@ -30,6 +33,12 @@
 #include "ff_core.cuh"
 #include "ff_host.cuh"
 
+// Internal record kind: rows of a GEMV instance, one warp per row.
+constexpr int32_t kGemvRows = 100;
+// GEMV rows up to this length are reduced by one warp each; longer rows
+// become dot records reduced by whole blocks over several tiles.
+constexpr int64_t kWarpRowMax = 65536;
+
 struct DevInst {
     const float2* x;
     const float2* y;
@@ -37,6 +46,8 @@ struct DevInst {
     float2* out2;
     const float2* dout;
     float2 alpha;
+    int64_t lda;   // GEMV rows: row stride of x
+    int64_t m;     // GEMV rows: number of rows
     int64_t n;
     int64_t first_tile;
     int32_t ntiles;
@@ -111,6 +122,41 @@ batch_kernel(const DevInst* __restrict__ insts, const Tile* __restrict__ tiles, 
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const Tile tl = tiles[t];
         const DevInst I = insts[tl.inst];
+        if (I.kind == kGemvRows) {
+            const int lane = threadIdx.x & 31;
+            const int64_t r = tl.start + (threadIdx.x >> 5);
+            if (r < I.m) {
+                const float2* Ar = I.x + r * I.lda;
+                float2 acc = make_float2(0.0f, 0.0f);
+                if (I.vec) {
+                    const float4* A4 = reinterpret_cast<const float4*>(Ar);
+                    const float4* x4 = reinterpret_cast<const float4*>(I.y);
+                    const int64_t nch = I.n >> 1;
+                    int64_t c = lane;
+                    for (; c + 32 < nch; c += 64) {
+                        const float4 a0 = __ldcs(A4 + c), a1 = __ldcs(A4 + c + 32);
+                        const float4 x0 = __ldg(x4 + c), x1 = __ldg(x4 + c + 32);
+                        acc = ffk::add22(acc, ffk::mul22(make_float2(a0.x, a0.y), make_float2(x0.x, x0.y)));
+                        acc = ffk::add22(acc, ffk::mul22(make_float2(a0.z, a0.w), make_float2(x0.z, x0.w)));
+                        acc = ffk::add22(acc, ffk::mul22(make_float2(a1.x, a1.y), make_float2(x1.x, x1.y)));
+                        acc = ffk::add22(acc, ffk::mul22(make_float2(a1.z, a1.w), make_float2(x1.z, x1.w)));
+                    }
+                    for (; c < nch; c += 32) {
+                        const float4 a0 = __ldcs(A4 + c);
+                        const float4 x0 = __ldg(x4 + c);
+                        acc = ffk::add22(acc, ffk::mul22(make_float2(a0.x, a0.y), make_float2(x0.x, x0.y)));
+                        acc = ffk::add22(acc, ffk::mul22(make_float2(a0.z, a0.w), make_float2(x0.z, x0.w)));
+                    }
+                    if ((I.n & 1) && lane == 0) acc = ffk::add22(acc, ffk::mul22(Ar[I.n - 1], I.y[I.n - 1]));
+                } else {
+                    for (int64_t j = lane; j < I.n; j += 32) acc = ffk::add22(acc, ffk::mul22(Ar[j], I.y[j]));
+                }
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) acc = ffk::add22(acc, shfl_down2(acc, off));
+                if (lane == 0) I.out[r] = acc;
+            }
+            continue;
+        }
         const int64_t s0 = tl.start;
         const int64_t s1 = min(s0 + static_cast<int64_t>(BLOCK) * PPT, I.n);
         if (I.kind == FF_BATCH_DOT) {
@@ -351,16 +397,20 @@ ff_status ff_batch_plan_create(const ff_batch_instance* inst, int count, const f
         void* out2;
         const void* dout;
         ff2 alpha;
+        int64_t lda;
+        int64_t m;
     };
     std::vector<Rec> recs;
     recs.reserve(static_cast<size_t>(count));
     for (int i = 0; i < count; ++i) {
         const ff_batch_instance& b = inst[i];
-        if (b.kind == FF_BATCH_GEMV) {
+        if (b.kind == FF_BATCH_GEMV && b.n <= kWarpRowMax) {
+            if (b.m > 0) recs.push_back(Rec{kGemvRows, b.n, b.x, b.y, b.out, nullptr, nullptr, b.alpha, b.lda, b.m});
+        } else if (b.kind == FF_BATCH_GEMV) {
             for (int64_t r = 0; r < b.m; ++r)
-                recs.push_back(Rec{FF_BATCH_DOT, b.n, b.x + r * b.lda, b.y, b.out + r, nullptr, nullptr, b.alpha});
+                recs.push_back(Rec{FF_BATCH_DOT, b.n, b.x + r * b.lda, b.y, b.out + r, nullptr, nullptr, b.alpha, 0, 0});
         } else {
-            recs.push_back(Rec{b.kind, b.n, b.x, b.y, b.out, b.out2, b.dout, b.alpha});
+            recs.push_back(Rec{b.kind, b.n, b.x, b.y, b.out, b.out2, b.dout, b.alpha, 0, 0});
         }
     }
     if (recs.size() > static_cast<size_t>(INT32_MAX)) return FF_ERR_INVALID_ARG;
@@ -378,15 +428,29 @@ ff_status ff_batch_plan_create(const ff_batch_instance* inst, int count, const f
         d.alpha = make_float2(b.alpha.hi, b.alpha.lo);
         d.n = b.n;
         d.kind = b.kind;
+        d.lda = b.lda;
+        d.m = b.m;
+        d.first_tile = static_cast<int64_t>(ht.size());
+        d.pad = 0;
+        if (b.kind == kGemvRows) {
+            // rows of 16-byte-aligned storage when the matrix, its row stride
+            // and the vector allow it
+            d.vec = (ffh::aligned(b.x, 16) && ffh::aligned(b.y, 16) && (b.lda % 2 == 0)) ? 1 : 0;
+            const int64_t warps = tune.block / 32;
+            const int64_t nt = (b.m + warps - 1) / warps;
+            if (nt > INT32_MAX) return FF_ERR_INVALID_ARG;
+            d.ntiles = static_cast<int32_t>(nt);
+            for (int64_t k = 0; k < nt; ++k) ht.push_back(Tile{static_cast<int32_t>(i), 0, k * warps});
+            total += b.m * b.n;
+            continue;
+        }
         d.vec = (ffh::aligned(b.x, 16) && ffh::aligned(b.y, 16) &&
                  (b.kind == FF_BATCH_DOT || ffh::aligned(b.out, 16)) &&
                  (b.kind != FF_BATCH_DOT_GRAD || ffh::aligned(b.out2, 16))) ? 1 : 0;
-        d.first_tile = static_cast<int64_t>(ht.size());
         // a dot of length 0 still needs one tile to write its (0, 0)
         const int64_t nt = b.n > 0 ? (b.n + tile - 1) / tile : (b.kind == FF_BATCH_DOT ? 1 : 0);
         if (nt > INT32_MAX) return FF_ERR_INVALID_ARG;
         d.ntiles = static_cast<int32_t>(nt);
-        d.pad = 0;
         for (int64_t k = 0; k < nt; ++k) ht.push_back(Tile{static_cast<int32_t>(i), 0, k * tile});
         ndot += (b.kind == FF_BATCH_DOT);
         total += b.n;
@@ -533,7 +597,7 @@ size_t ff_batch_autotune_workspace_bytes(const ff_batch_instance* inst, int coun
     size_t ntiles = 0, nrec = 0;
     for (int i = 0; i < count; ++i) {
         const int64_t n = inst[i].n;
-        const size_t reps = inst[i].kind == FF_BATCH_GEMV ? static_cast<size_t>(inst[i].m > 0 ? inst[i].m : 0) : 1;
+        const size_t reps = (inst[i].kind == FF_BATCH_GEMV) ? static_cast<size_t>(inst[i].m > 0 ? inst[i].m : 0) : 1;
         ntiles += reps * static_cast<size_t>(n > 0 ? (n + smallest - 1) / smallest : 1);
         nrec += reps;
     }

@@ -164,13 +164,14 @@ def test_batch_errors():
     plan.close()
 
 
-def test_batch_gemv_instances():
+@pytest.mark.parametrize("tune", [None, (128, 16, 0), (512, 64, 2)])
+def test_batch_gemv_instances(tune):
     """GEMV instances of uneven shapes (rows become dot records) mixed with
     dots and AXPYs: every row within the dot bound of the exact value, and
     equal to the plain ff_gemv within twice the bound."""
     import paper_cs_0603115_gb300 as ff
     from paper_cs_0603115_gb300 import batch
-    shapes = [(1, 1), (3, 1000), (17, 4097), (64, 9), (0, 5), (5, 0), (40, 20001)]
+    shapes = [(1, 1), (3, 1000), (17, 4097), (64, 9), (0, 5), (5, 0), (40, 20001), (3, 70001), (2, 65536)]
     specs, keep = [], []
     for i, (m, n) in enumerate(shapes):
         gi = inputs.gemv(m, n, 1, inputs.seed_for(4, 70 + i))
@@ -179,7 +180,7 @@ def test_batch_gemv_instances():
         specs.append((batch.GEMV, A, x, out, None))
         keep.append((gi.A.numpy(), gi.X[0].numpy(), A, x, out))
     dspecs, dkeep = build_case([100, 7, 4097], [batch.DOT, batch.AXPY, batch.DOT], 8000)
-    plan = batch.BatchPlan(batch.make_instances(specs + dspecs)).capture()
+    plan = batch.BatchPlan(batch.make_instances(specs + dspecs), tune=tune).capture()
     plan.launch()
     torch.cuda.synchronize()
     check(dkeep)
