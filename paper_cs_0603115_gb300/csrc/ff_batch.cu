@@ -13,9 +13,11 @@
 //   AXPY tile: z_i = Add22(Mul22(alpha, x_i), y_i) for the tile's values.
 //   dot-gradient tile: dx_i = Mul22(dout, y_i), dy_i = Mul22(dout, x_i).
 //   GEMV rows tile (rows of length <= 65536): warp w of the block reduces
-//   row start + w: lane l accumulates the two-value chunks l, l + 32, ... of
-//   the row with Add22(acc, Mul22(A_rj, x_j)), the warp combines its lanes
-//   with the shuffle-down Add22 tree and lane 0 writes out[r].  Longer GEMV
+//   row start + w.  Lane l accumulates the row's two-value chunks with
+//   Add22(acc, Mul22(A_rj, x_j)) into two accumulators (chunks l + 128i and
+//   l + 64 + 128i into the first, l + 32 + 128i and l + 96 + 128i into the
+//   second, leftover chunks into the first), adds them, the warp combines
+//   its lanes with the shuffle-down Add22 tree and lane 0 writes out[r].  Longer GEMV
 //   rows become dot records (row r of the matrix with the vector).
 //   dot tile:  each thread accumulates its values left to right with
 //              Add22(acc, Mul22(x_i, y_i)); the block combines threads with
@@ -129,17 +131,25 @@ batch_kernel(const DevInst* __restrict__ insts, const Tile* __restrict__ tiles, 
                 const float2* Ar = I.x + r * I.lda;
                 float2 acc = make_float2(0.0f, 0.0f);
                 if (I.vec) {
+                    // four chunks in flight per lane, two accumulators
                     const float4* A4 = reinterpret_cast<const float4*>(Ar);
                     const float4* x4 = reinterpret_cast<const float4*>(I.y);
                     const int64_t nch = I.n >> 1;
+                    float2 acc1 = make_float2(0.0f, 0.0f);
                     int64_t c = lane;
-                    for (; c + 32 < nch; c += 64) {
-                        const float4 a0 = __ldcs(A4 + c), a1 = __ldcs(A4 + c + 32);
-                        const float4 x0 = __ldg(x4 + c), x1 = __ldg(x4 + c + 32);
-                        acc = ffk::add22(acc, ffk::mul22(make_float2(a0.x, a0.y), make_float2(x0.x, x0.y)));
-                        acc = ffk::add22(acc, ffk::mul22(make_float2(a0.z, a0.w), make_float2(x0.z, x0.w)));
-                        acc = ffk::add22(acc, ffk::mul22(make_float2(a1.x, a1.y), make_float2(x1.x, x1.y)));
-                        acc = ffk::add22(acc, ffk::mul22(make_float2(a1.z, a1.w), make_float2(x1.z, x1.w)));
+                    for (; c + 96 < nch; c += 128) {
+                        float4 a[4], x[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            a[q] = __ldcs(A4 + c + 32 * q);
+                            x[q] = __ldg(x4 + c + 32 * q);
+                        }
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            float2& ac = (q & 1) ? acc1 : acc;
+                            ac = ffk::add22(ac, ffk::mul22(make_float2(a[q].x, a[q].y), make_float2(x[q].x, x[q].y)));
+                            ac = ffk::add22(ac, ffk::mul22(make_float2(a[q].z, a[q].w), make_float2(x[q].z, x[q].w)));
+                        }
                     }
                     for (; c < nch; c += 32) {
                         const float4 a0 = __ldcs(A4 + c);
@@ -147,6 +157,7 @@ batch_kernel(const DevInst* __restrict__ insts, const Tile* __restrict__ tiles, 
                         acc = ffk::add22(acc, ffk::mul22(make_float2(a0.x, a0.y), make_float2(x0.x, x0.y)));
                         acc = ffk::add22(acc, ffk::mul22(make_float2(a0.z, a0.w), make_float2(x0.z, x0.w)));
                     }
+                    acc = ffk::add22(acc, acc1);
                     if ((I.n & 1) && lane == 0) acc = ffk::add22(acc, ffk::mul22(Ar[I.n - 1], I.y[I.n - 1]));
                 } else {
                     for (int64_t j = lane; j < I.n; j += 32) acc = ffk::add22(acc, ffk::mul22(Ar[j], I.y[j]));
