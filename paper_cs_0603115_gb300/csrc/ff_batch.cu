@@ -13,7 +13,8 @@
 //   AXPY tile: z_i = Add22(Mul22(alpha, x_i), y_i) for the tile's values.
 //   dot-gradient tile: dx_i = Mul22(dout, y_i), dy_i = Mul22(dout, x_i).
 //   GEMV rows tile (rows of length <= 65536): warp w of the block reduces
-//   row start + w.  Lane l accumulates the row's two-value chunks with
+//   rows start + w R .. start + w R + R - 1 in turn (R rows per warp, chosen
+//   at plan time so that a tile holds about 16K values).  Lane l accumulates the row's two-value chunks with
 //   Add22(acc, Mul22(A_rj, x_j)) into two accumulators (chunks l + 128i and
 //   l + 64 + 128i into the first, l + 32 + 128i and l + 96 + 128i into the
 //   second, leftover chunks into the first), adds them, the warp combines
@@ -55,7 +56,7 @@ struct DevInst {
     int32_t ntiles;
     int32_t kind;
     int32_t vec;
-    int32_t pad;
+    int32_t rows_per_warp;  // GEMV rows: rows each warp reduces per tile
 };
 
 struct Tile {
@@ -126,7 +127,9 @@ batch_kernel(const DevInst* __restrict__ insts, const Tile* __restrict__ tiles, 
         const DevInst I = insts[tl.inst];
         if (I.kind == kGemvRows) {
             const int lane = threadIdx.x & 31;
-            const int64_t r = tl.start + (threadIdx.x >> 5);
+            const int rpw = I.rows_per_warp;
+            for (int k = 0; k < rpw; ++k) {
+            const int64_t r = tl.start + static_cast<int64_t>(threadIdx.x >> 5) * rpw + k;
             if (r < I.m) {
                 const float2* Ar = I.x + r * I.lda;
                 float2 acc = make_float2(0.0f, 0.0f);
@@ -165,6 +168,7 @@ batch_kernel(const DevInst* __restrict__ insts, const Tile* __restrict__ tiles, 
 #pragma unroll
                 for (int off = 16; off > 0; off >>= 1) acc = ffk::add22(acc, shfl_down2(acc, off));
                 if (lane == 0) I.out[r] = acc;
+            }
             }
             continue;
         }
@@ -442,16 +446,20 @@ ff_status ff_batch_plan_create(const ff_batch_instance* inst, int count, const f
         d.lda = b.lda;
         d.m = b.m;
         d.first_tile = static_cast<int64_t>(ht.size());
-        d.pad = 0;
+        d.rows_per_warp = 0;
         if (b.kind == kGemvRows) {
             // rows of 16-byte-aligned storage when the matrix, its row stride
             // and the vector allow it
             d.vec = (ffh::aligned(b.x, 16) && ffh::aligned(b.y, 16) && (b.lda % 2 == 0)) ? 1 : 0;
             const int64_t warps = tune.block / 32;
-            const int64_t nt = (b.m + warps - 1) / warps;
+            int64_t rpw = 16384 / (warps * (b.n > 0 ? b.n : 1));
+            rpw = rpw < 1 ? 1 : (rpw > 16 ? 16 : rpw);
+            d.rows_per_warp = static_cast<int32_t>(rpw);
+            const int64_t rows_per_tile = warps * rpw;
+            const int64_t nt = (b.m + rows_per_tile - 1) / rows_per_tile;
             if (nt > INT32_MAX) return FF_ERR_INVALID_ARG;
             d.ntiles = static_cast<int32_t>(nt);
-            for (int64_t k = 0; k < nt; ++k) ht.push_back(Tile{static_cast<int32_t>(i), 0, k * warps});
+            for (int64_t k = 0; k < nt; ++k) ht.push_back(Tile{static_cast<int32_t>(i), 0, k * rows_per_tile});
             total += b.m * b.n;
             continue;
         }
