@@ -120,11 +120,11 @@ batch_kernel(const DevInst* __restrict__ insts, const Tile* __restrict__ tiles, 
     __shared__ float2 sm[BLOCK / 32];
     __shared__ int is_last;
     constexpr int CH = PPT / 2;   // chunks per thread per tile
-    constexpr int U = CH < 4 ? CH : 4;
+    constexpr int U = CH < 2 ? CH : 2;
 
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const Tile tl = tiles[t];
-        const DevInst I = insts[tl.inst];
+        const DevInst& I = insts[tl.inst];
         if (I.kind == kGemvRows) {
             const int lane = threadIdx.x & 31;
             const int rpw = I.rows_per_warp;
@@ -134,21 +134,21 @@ batch_kernel(const DevInst* __restrict__ insts, const Tile* __restrict__ tiles, 
                 const float2* Ar = I.x + r * I.lda;
                 float2 acc = make_float2(0.0f, 0.0f);
                 if (I.vec) {
-                    // four chunks in flight per lane, two accumulators
+                    // two chunks in flight per lane, two accumulators
                     const float4* A4 = reinterpret_cast<const float4*>(Ar);
                     const float4* x4 = reinterpret_cast<const float4*>(I.y);
                     const int64_t nch = I.n >> 1;
                     float2 acc1 = make_float2(0.0f, 0.0f);
                     int64_t c = lane;
-                    for (; c + 96 < nch; c += 128) {
-                        float4 a[4], x[4];
+                    for (; c + 32 < nch; c += 64) {
+                        float4 a[2], x[2];
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
+                        for (int q = 0; q < 2; ++q) {
                             a[q] = __ldcs(A4 + c + 32 * q);
                             x[q] = __ldg(x4 + c + 32 * q);
                         }
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
+                        for (int q = 0; q < 2; ++q) {
                             float2& ac = (q & 1) ? acc1 : acc;
                             ac = ffk::add22(ac, ffk::mul22(make_float2(a[q].x, a[q].y), make_float2(x[q].x, x[q].y)));
                             ac = ffk::add22(ac, ffk::mul22(make_float2(a[q].z, a[q].w), make_float2(x[q].z, x[q].w)));
