@@ -266,12 +266,14 @@ typedef struct ff_batch_instance {
 
 /* Launch configuration of the batched kernel: threads per block (128, 256
  * or 512), values per thread per tile (pairs_per_thread: 8 .. 128, tile =
- * block x pairs_per_thread values) and resident blocks per SM (0 = as many
- * as fit). */
+ * block x pairs_per_thread values), resident blocks per SM (0 = as many as
+ * fit) and two-value chunks per input loaded ahead of use (unroll: 2 or 4;
+ * 0 = 4). */
 typedef struct ff_tune {
     int32_t block;
     int32_t pairs_per_thread;
     int32_t blocks_per_sm;
+    int32_t unroll;
 } ff_tune;
 
 typedef struct ff_batch_plan ff_batch_plan;
@@ -280,7 +282,7 @@ typedef struct ff_batch_graph ff_batch_graph;
 /* Build a plan on the current device: cut every instance into tiles and copy
  * the instance records and the tile list to device memory the plan owns
  * (the only allocation of the library, made here, never in a run).
- * tune_or_null == NULL uses {256, 32, 0}.  Unsupported tunes return
+ * tune_or_null == NULL uses {256, 32, 0, 4}.  Unsupported tunes return
  * FF_ERR_INVALID_ARG. */
 FF_API ff_status ff_batch_plan_create(const ff_batch_instance* inst, int count, const ff_tune* tune_or_null,
                                       ff_batch_plan** out);

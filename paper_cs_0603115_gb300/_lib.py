@@ -28,7 +28,8 @@ class ff_batch_instance(ctypes.Structure):
 
 
 class ff_tune(ctypes.Structure):
-    _fields_ = [("block", ctypes.c_int32), ("pairs_per_thread", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32)]
+    _fields_ = [("block", ctypes.c_int32), ("pairs_per_thread", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("unroll", ctypes.c_int32)]
 
 
 P = ctypes.c_void_p

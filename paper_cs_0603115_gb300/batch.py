@@ -74,7 +74,7 @@ class BatchPlan:
         ntiles = ctypes.c_int64()
         grid = ctypes.c_uint()
         _lib.call("ff_batch_plan_info", handle, ctypes.byref(info), ctypes.byref(ntiles), ctypes.byref(grid))
-        self.tune = (info.block, info.pairs_per_thread, info.blocks_per_sm)
+        self.tune = (info.block, info.pairs_per_thread, info.blocks_per_sm, info.unroll)
         self.ntiles = ntiles.value
         self.grid = grid.value
 
@@ -125,7 +125,7 @@ def _cache_key(instances) -> str:
 
 
 def autotune(instances, reps: int = 3, cache_path: str | None = DEFAULT_CACHE, force: bool = False):
-    """Pick (block, pairs_per_thread, blocks_per_sm) for these instances.
+    """Pick (block, pairs_per_thread, blocks_per_sm, unroll) for these instances.
 
     Looks the workload's key up in the JSON cache first; otherwise times
     every candidate natively (the instances' outputs are overwritten) and
@@ -147,7 +147,7 @@ def autotune(instances, reps: int = 3, cache_path: str | None = DEFAULT_CACHE, f
     ms = ctypes.c_float()
     _lib.call("ff_batch_autotune", instances, len(instances), ws.data_ptr(), ws.numel(),
               torch.cuda.current_stream().cuda_stream, reps, ctypes.byref(best), ctypes.byref(ms))
-    tune = (best.block, best.pairs_per_thread, best.blocks_per_sm)
+    tune = (best.block, best.pairs_per_thread, best.blocks_per_sm, best.unroll)
     if cache_path:
         cache[key] = {"tune": list(tune), "ms": ms.value}
         os.makedirs(os.path.dirname(cache_path), exist_ok=True)
@@ -163,4 +163,4 @@ def candidates():
     n = L.ff_batch_tune_candidates(None, 0)
     arr = (ff_tune * n)()
     L.ff_batch_tune_candidates(arr, n)
-    return [(c.block, c.pairs_per_thread, c.blocks_per_sm) for c in arr]
+    return [(c.block, c.pairs_per_thread, c.blocks_per_sm, c.unroll) for c in arr]

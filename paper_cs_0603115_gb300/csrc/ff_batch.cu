@@ -111,8 +111,10 @@ __device__ __forceinline__ float2 block_reduce(float2 v, float2* sm)
 }
 
 // PPT values per thread per tile (even).  Values of a tile are visited as
-// two-value chunks c = threadIdx.x + j * BLOCK, j = 0 .. PPT/2 - 1.
-template <int BLOCK, int PPT>
+// two-value chunks c = threadIdx.x + j * BLOCK, j = 0 .. PPT/2 - 1, UN
+// chunks per input loaded before they are used (UN = 4 keeps more bytes in
+// flight per thread, UN = 2 needs fewer registers and so fits more warps).
+template <int BLOCK, int PPT, int UN>
 __global__ void __launch_bounds__(BLOCK)
 batch_kernel(const DevInst* __restrict__ insts, const Tile* __restrict__ tiles, int64_t ntiles,
              float2* __restrict__ partials, unsigned* __restrict__ counters)
@@ -120,7 +122,7 @@ batch_kernel(const DevInst* __restrict__ insts, const Tile* __restrict__ tiles, 
     __shared__ float2 sm[BLOCK / 32];
     __shared__ int is_last;
     constexpr int CH = PPT / 2;   // chunks per thread per tile
-    constexpr int U = CH < 2 ? CH : 2;
+    constexpr int U = CH < UN ? CH : UN;
 
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const Tile tl = tiles[t];
@@ -331,25 +333,31 @@ using KernelFn = void (*)(const DevInst*, const Tile*, int64_t, float2*, unsigne
 struct Variant {
     int block;
     int ppt;
+    int unroll;
     KernelFn fn;
 };
 
-const Variant kVariants[] = {
-    {128, 16, batch_kernel<128, 16>}, {128, 32, batch_kernel<128, 32>}, {128, 64, batch_kernel<128, 64>},
-    {128, 128, batch_kernel<128, 128>}, {256, 8, batch_kernel<256, 8>}, {256, 16, batch_kernel<256, 16>},
-    {256, 32, batch_kernel<256, 32>}, {256, 64, batch_kernel<256, 64>}, {256, 128, batch_kernel<256, 128>},
-    {512, 8, batch_kernel<512, 8>}, {512, 16, batch_kernel<512, 16>}, {512, 32, batch_kernel<512, 32>},
-    {512, 64, batch_kernel<512, 64>},
-};
+#define FF_BATCH_VARIANTS(UN)                                                                              \
+    {128, 16, UN, batch_kernel<128, 16, UN>}, {128, 32, UN, batch_kernel<128, 32, UN>},                      \
+        {128, 64, UN, batch_kernel<128, 64, UN>}, {128, 128, UN, batch_kernel<128, 128, UN>},                \
+        {256, 8, UN, batch_kernel<256, 8, UN>}, {256, 16, UN, batch_kernel<256, 16, UN>},                    \
+        {256, 32, UN, batch_kernel<256, 32, UN>}, {256, 64, UN, batch_kernel<256, 64, UN>},                  \
+        {256, 128, UN, batch_kernel<256, 128, UN>}, {512, 8, UN, batch_kernel<512, 8, UN>},                  \
+        {512, 16, UN, batch_kernel<512, 16, UN>}, {512, 32, UN, batch_kernel<512, 32, UN>},                  \
+        {512, 64, UN, batch_kernel<512, 64, UN>}
 
-const Variant* find_variant(int block, int ppt)
+const Variant kVariants[] = {FF_BATCH_VARIANTS(4), FF_BATCH_VARIANTS(2)};
+#undef FF_BATCH_VARIANTS
+
+const Variant* find_variant(const ff_tune& t)
 {
+    const int un = t.unroll == 0 ? 4 : t.unroll;
     for (const Variant& v : kVariants)
-        if (v.block == block && v.ppt == ppt) return &v;
+        if (v.block == t.block && v.ppt == t.pairs_per_thread && v.unroll == un) return &v;
     return nullptr;
 }
 
-const ff_tune kDefaultTune = {256, 32, 0};
+const ff_tune kDefaultTune = {256, 32, 0, 4};
 
 size_t ws_bytes_for(const ff_batch_plan* p)
 {
@@ -395,7 +403,7 @@ ff_status ff_batch_plan_create(const ff_batch_instance* inst, int count, const f
     ff_status st = validate(inst, count);
     if (st != FF_OK) return st;
     ff_tune tune = tune_or_null ? *tune_or_null : kDefaultTune;
-    const Variant* var = find_variant(tune.block, tune.pairs_per_thread);
+    const Variant* var = find_variant(tune);
     if (!var || tune.blocks_per_sm < 0 || tune.blocks_per_sm > 32) return FF_ERR_INVALID_ARG;
     ffh::DeviceInfo di;
     st = ffh::device_info(&di);
@@ -524,7 +532,7 @@ ff_status ff_batch_run(const ff_batch_plan* p, void* ws, size_t ws_bytes, cudaSt
     if (ws == nullptr || ws_bytes < ws_bytes_for(p) || !ffh::aligned(ws, 16)) return FF_ERR_WORKSPACE;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != p->device) return FF_ERR_INVALID_ARG;
-    const Variant* var = find_variant(p->tune.block, p->tune.pairs_per_thread);
+    const Variant* var = find_variant(p->tune);
     if (!var) return FF_ERR_INVALID_ARG;
     auto* counters = static_cast<unsigned*>(ws);
     const size_t cbytes = ((static_cast<size_t>(p->count) * 4 + kCountersAlign - 1) / kCountersAlign) * kCountersAlign;
@@ -601,7 +609,7 @@ int ff_batch_tune_candidates(ff_tune* out, int max)
     int k = 0;
     for (const Variant& v : kVariants)
         for (int b = 0; b < per; ++b) {
-            if (out && k < max) out[k] = ff_tune{v.block, v.ppt, bps[b]};
+            if (out && k < max) out[k] = ff_tune{v.block, v.ppt, bps[b], v.unroll};
             ++k;
         }
     return k;

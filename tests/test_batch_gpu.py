@@ -76,7 +76,7 @@ LENGTHS = [0, 1, 2, 3, 7, 100, 1000, 4095, 4096, 4097, 8191, 8192, 20001, 65536,
            33, 777, 3000, 12345, 54321, 99999]
 
 
-@pytest.mark.parametrize("tune", [None, (128, 16, 0), (256, 64, 2), (512, 8, 4), (512, 64, 0)])
+@pytest.mark.parametrize("tune", [None, (128, 16, 0), (256, 64, 2), (512, 8, 4), (512, 64, 0), (256, 32, 0, 2), (128, 128, 2, 2)])
 def test_batch_run_matches_oracle(tune):
     from paper_cs_0603115_gb300 import batch
     kinds = [batch.DOT if i % 2 else batch.AXPY for i in range(len(LENGTHS))]
@@ -164,7 +164,7 @@ def test_batch_errors():
     plan.close()
 
 
-@pytest.mark.parametrize("tune", [None, (128, 16, 0), (512, 64, 2)])
+@pytest.mark.parametrize("tune", [None, (128, 16, 0), (512, 64, 2), (256, 32, 0, 2)])
 def test_batch_gemv_instances(tune):
     """GEMV instances of uneven shapes (rows become dot records) mixed with
     dots and AXPYs: every row within the dot bound of the exact value, and
