@@ -126,7 +126,7 @@ batch_kernel(const DevInst* __restrict__ insts, const Tile* __restrict__ tiles, 
 
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const Tile tl = tiles[t];
-        const DevInst& I = insts[tl.inst];
+        const DevInst I = insts[tl.inst];
         if (I.kind == kGemvRows) {
             const int lane = threadIdx.x & 31;
             const int rpw = I.rows_per_warp;
