@@ -110,6 +110,51 @@ __device__ __forceinline__ float2 block_reduce(float2 v, float2* sm)
     return v;
 }
 
+// One tile of GEMV rows (see the header comment): rows start + w R ..
+// start + w R + R - 1 for warp w.  Kept out of line, with its arguments by
+// value, so that its registers and code do not weigh on the dot / AXPY /
+// gradient sweep of the kernel.
+__device__ __noinline__ void gemv_rows_tile(const float2* A, const float2* xv, float2* out, int64_t n,
+                                            int64_t lda, int64_t m, int vec, int rpw, int64_t start)
+{
+    const int lane = threadIdx.x & 31;
+    for (int k = 0; k < rpw; ++k) {
+        const int64_t r = start + static_cast<int64_t>(threadIdx.x >> 5) * rpw + k;
+        if (r >= m) break;
+        const float2* Ar = A + r * lda;
+        float2 acc = make_float2(0.0f, 0.0f);
+        if (vec) {
+            // two chunks in flight per lane, two accumulators
+            const float4* A4 = reinterpret_cast<const float4*>(Ar);
+            const float4* x4 = reinterpret_cast<const float4*>(xv);
+            const int64_t nch = n >> 1;
+            float2 acc1 = make_float2(0.0f, 0.0f);
+            int64_t c = lane;
+            for (; c + 32 < nch; c += 64) {
+                const float4 a0 = __ldcs(A4 + c), a1 = __ldcs(A4 + c + 32);
+                const float4 x0 = __ldg(x4 + c), x1 = __ldg(x4 + c + 32);
+                acc = ffk::add22(acc, ffk::mul22(make_float2(a0.x, a0.y), make_float2(x0.x, x0.y)));
+                acc = ffk::add22(acc, ffk::mul22(make_float2(a0.z, a0.w), make_float2(x0.z, x0.w)));
+                acc1 = ffk::add22(acc1, ffk::mul22(make_float2(a1.x, a1.y), make_float2(x1.x, x1.y)));
+                acc1 = ffk::add22(acc1, ffk::mul22(make_float2(a1.z, a1.w), make_float2(x1.z, x1.w)));
+            }
+            for (; c < nch; c += 32) {
+                const float4 a0 = __ldcs(A4 + c);
+                const float4 x0 = __ldg(x4 + c);
+                acc = ffk::add22(acc, ffk::mul22(make_float2(a0.x, a0.y), make_float2(x0.x, x0.y)));
+                acc = ffk::add22(acc, ffk::mul22(make_float2(a0.z, a0.w), make_float2(x0.z, x0.w)));
+            }
+            acc = ffk::add22(acc, acc1);
+            if ((n & 1) && lane == 0) acc = ffk::add22(acc, ffk::mul22(Ar[n - 1], xv[n - 1]));
+        } else {
+            for (int64_t j = lane; j < n; j += 32) acc = ffk::add22(acc, ffk::mul22(Ar[j], xv[j]));
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc = ffk::add22(acc, shfl_down2(acc, off));
+        if (lane == 0) out[r] = acc;
+    }
+}
+
 // PPT values per thread per tile (even).  Values of a tile are visited as
 // two-value chunks c = threadIdx.x + j * BLOCK, j = 0 .. PPT/2 - 1, UN
 // chunks per input loaded before they are used (UN = 4 keeps more bytes in
@@ -128,50 +173,7 @@ batch_kernel(const DevInst* __restrict__ insts, const Tile* __restrict__ tiles, 
         const Tile tl = tiles[t];
         const DevInst I = insts[tl.inst];
         if (I.kind == kGemvRows) {
-            const int lane = threadIdx.x & 31;
-            const int rpw = I.rows_per_warp;
-            for (int k = 0; k < rpw; ++k) {
-            const int64_t r = tl.start + static_cast<int64_t>(threadIdx.x >> 5) * rpw + k;
-            if (r < I.m) {
-                const float2* Ar = I.x + r * I.lda;
-                float2 acc = make_float2(0.0f, 0.0f);
-                if (I.vec) {
-                    // two chunks in flight per lane, two accumulators
-                    const float4* A4 = reinterpret_cast<const float4*>(Ar);
-                    const float4* x4 = reinterpret_cast<const float4*>(I.y);
-                    const int64_t nch = I.n >> 1;
-                    float2 acc1 = make_float2(0.0f, 0.0f);
-                    int64_t c = lane;
-                    for (; c + 32 < nch; c += 64) {
-                        float4 a[2], x[2];
-#pragma unroll
-                        for (int q = 0; q < 2; ++q) {
-                            a[q] = __ldcs(A4 + c + 32 * q);
-                            x[q] = __ldg(x4 + c + 32 * q);
-                        }
-#pragma unroll
-                        for (int q = 0; q < 2; ++q) {
-                            float2& ac = (q & 1) ? acc1 : acc;
-                            ac = ffk::add22(ac, ffk::mul22(make_float2(a[q].x, a[q].y), make_float2(x[q].x, x[q].y)));
-                            ac = ffk::add22(ac, ffk::mul22(make_float2(a[q].z, a[q].w), make_float2(x[q].z, x[q].w)));
-                        }
-                    }
-                    for (; c < nch; c += 32) {
-                        const float4 a0 = __ldcs(A4 + c);
-                        const float4 x0 = __ldg(x4 + c);
-                        acc = ffk::add22(acc, ffk::mul22(make_float2(a0.x, a0.y), make_float2(x0.x, x0.y)));
-                        acc = ffk::add22(acc, ffk::mul22(make_float2(a0.z, a0.w), make_float2(x0.z, x0.w)));
-                    }
-                    acc = ffk::add22(acc, acc1);
-                    if ((I.n & 1) && lane == 0) acc = ffk::add22(acc, ffk::mul22(Ar[I.n - 1], I.y[I.n - 1]));
-                } else {
-                    for (int64_t j = lane; j < I.n; j += 32) acc = ffk::add22(acc, ffk::mul22(Ar[j], I.y[j]));
-                }
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) acc = ffk::add22(acc, shfl_down2(acc, off));
-                if (lane == 0) I.out[r] = acc;
-            }
-            }
+            gemv_rows_tile(I.x, I.y, I.out, I.n, I.lda, I.m, I.vec, I.rows_per_warp, tl.start);
             continue;
         }
         const int64_t s0 = tl.start;
