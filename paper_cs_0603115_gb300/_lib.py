@@ -12,7 +12,9 @@ import os
 import re
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libff.so")
+# FF_LIBRARY may name another build of the same sources (e.g. a variant
+# compiled with different flags); by default the in-tree libff.so
+LIB_PATH = os.environ.get("FF_LIBRARY") or os.path.join(HERE, "libff.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "ff.h")
 
 

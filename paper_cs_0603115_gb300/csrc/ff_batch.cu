@@ -67,6 +67,7 @@ struct Tile {
 
 struct ff_batch_plan {
     int count;
+    bool has_gemv_rows;
     ff_tune tune;
     int64_t ntiles;
     int64_t ndot;
@@ -159,7 +160,7 @@ __device__ __noinline__ void gemv_rows_tile(const float2* A, const float2* xv, f
 // two-value chunks c = threadIdx.x + j * BLOCK, j = 0 .. PPT/2 - 1, UN
 // chunks per input loaded before they are used (UN = 4 keeps more bytes in
 // flight per thread, UN = 2 needs fewer registers and so fits more warps).
-template <int BLOCK, int PPT, int UN>
+template <int BLOCK, int PPT, int UN, bool GEMV_ROWS>
 __global__ void __launch_bounds__(BLOCK)
 batch_kernel(const DevInst* __restrict__ insts, const Tile* __restrict__ tiles, int64_t ntiles,
              float2* __restrict__ partials, unsigned* __restrict__ counters)
@@ -172,7 +173,10 @@ batch_kernel(const DevInst* __restrict__ insts, const Tile* __restrict__ tiles, 
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const Tile tl = tiles[t];
         const DevInst I = insts[tl.inst];
-        if (I.kind == kGemvRows) {
+        // compiled only into the kernels used by plans that hold GEMV rows:
+        // its presence measurably slows the other paths (about 7% on the best
+        // launch shape, 45% on the default one)
+        if (GEMV_ROWS && I.kind == kGemvRows) {
             gemv_rows_tile(I.x, I.y, I.out, I.n, I.lda, I.m, I.vec, I.rows_per_warp, tl.start);
             continue;
         }
@@ -336,19 +340,18 @@ struct Variant {
     int block;
     int ppt;
     int unroll;
-    KernelFn fn;
+    KernelFn fn;        // plans without GEMV rows
+    KernelFn fn_gemv;   // plans with GEMV rows
 };
 
+#define FF_BV(B, P, UN) {B, P, UN, batch_kernel<B, P, UN, false>, batch_kernel<B, P, UN, true>}
 #define FF_BATCH_VARIANTS(UN)                                                                              \
-    {128, 16, UN, batch_kernel<128, 16, UN>}, {128, 32, UN, batch_kernel<128, 32, UN>},                      \
-        {128, 64, UN, batch_kernel<128, 64, UN>}, {128, 128, UN, batch_kernel<128, 128, UN>},                \
-        {256, 8, UN, batch_kernel<256, 8, UN>}, {256, 16, UN, batch_kernel<256, 16, UN>},                    \
-        {256, 32, UN, batch_kernel<256, 32, UN>}, {256, 64, UN, batch_kernel<256, 64, UN>},                  \
-        {256, 128, UN, batch_kernel<256, 128, UN>}, {512, 8, UN, batch_kernel<512, 8, UN>},                  \
-        {512, 16, UN, batch_kernel<512, 16, UN>}, {512, 32, UN, batch_kernel<512, 32, UN>},                  \
-        {512, 64, UN, batch_kernel<512, 64, UN>}
+    FF_BV(128, 16, UN), FF_BV(128, 32, UN), FF_BV(128, 64, UN), FF_BV(128, 128, UN), FF_BV(256, 8, UN),        \
+        FF_BV(256, 16, UN), FF_BV(256, 32, UN), FF_BV(256, 64, UN), FF_BV(256, 128, UN), FF_BV(512, 8, UN),    \
+        FF_BV(512, 16, UN), FF_BV(512, 32, UN), FF_BV(512, 64, UN)
 
 const Variant kVariants[] = {FF_BATCH_VARIANTS(4), FF_BATCH_VARIANTS(2)};
+#undef FF_BV
 #undef FF_BATCH_VARIANTS
 
 const Variant* find_variant(const ff_tune& t)
@@ -487,13 +490,16 @@ ff_status ff_batch_plan_create(const ff_batch_instance* inst, int count, const f
     auto* p = new (std::nothrow) ff_batch_plan();
     if (!p) return FF_ERR_UNSUPPORTED;
     p->count = static_cast<int>(recs.size());
+    p->has_gemv_rows = false;
+    for (const Rec& r : recs) p->has_gemv_rows |= (r.kind == kGemvRows);
     p->tune = tune;
     p->ntiles = static_cast<int64_t>(ht.size());
     p->ndot = ndot;
     p->total_values = total;
     p->device = di.device;
     int bps = tune.blocks_per_sm;
-    if (bps == 0) bps = ffh::occupancy(reinterpret_cast<const void*>(var->fn), tune.block);
+    if (bps == 0)
+        bps = ffh::occupancy(reinterpret_cast<const void*>(p->has_gemv_rows ? var->fn_gemv : var->fn), tune.block);
     int64_t grid = static_cast<int64_t>(di.sm_count) * (bps > 0 ? bps : 1);
     if (grid > p->ntiles) grid = p->ntiles > 0 ? p->ntiles : 1;
     p->grid = static_cast<unsigned>(grid);
@@ -541,7 +547,8 @@ ff_status ff_batch_run(const ff_batch_plan* p, void* ws, size_t ws_bytes, cudaSt
     auto* partials = reinterpret_cast<float2*>(static_cast<char*>(ws) + cbytes);
     ff_status st = ffh::cuda_status(cudaMemsetAsync(counters, 0, static_cast<size_t>(p->count) * 4, s));
     if (st != FF_OK) return st;
-    var->fn<<<p->grid, p->tune.block, 0, s>>>(p->d_inst, p->d_tiles, p->ntiles, partials, counters);
+    KernelFn fn = p->has_gemv_rows ? var->fn_gemv : var->fn;
+    fn<<<p->grid, p->tune.block, 0, s>>>(p->d_inst, p->d_tiles, p->ntiles, partials, counters);
     return ffh::check_launch();
 }
 
