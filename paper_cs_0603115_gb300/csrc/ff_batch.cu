@@ -111,48 +111,59 @@ __device__ __forceinline__ float2 block_reduce(float2 v, float2* sm)
     return v;
 }
 
-// One tile of GEMV rows (see the header comment): rows start + w R ..
-// start + w R + R - 1 for warp w.  Kept out of line, with its arguments by
-// value, so that its registers and code do not weigh on the dot / AXPY /
-// gradient sweep of the kernel.
+// One tile of GEMV rows (see the header comment).  Eight lanes reduce one
+// row, so a warp works on four rows at once: lane group g (lanes 8g .. 8g+7)
+// of warp w takes rows start + 4 (w R + k) + g for k = 0 .. R-1, lane l of
+// the group accumulates the row's two-value chunks l + 16i into its first
+// and l + 8 + 16i into its second accumulator (a leftover chunk into the
+// first), adds them, the group combines its eight lanes with a shuffle-down
+// Add22 tree (offsets 4, 2, 1) and its lane 0 writes out[r].  Kept out of
+// line, with its arguments by value.
 __device__ __noinline__ void gemv_rows_tile(const float2* A, const float2* xv, float2* out, int64_t n,
                                             int64_t lda, int64_t m, int vec, int rpw, int64_t start)
 {
     const int lane = threadIdx.x & 31;
+    const int g = lane >> 3;
+    const int l8 = lane & 7;
+    const int64_t w = threadIdx.x >> 5;
     for (int k = 0; k < rpw; ++k) {
-        const int64_t r = start + static_cast<int64_t>(threadIdx.x >> 5) * rpw + k;
-        if (r >= m) break;
-        const float2* Ar = A + r * lda;
+        const int64_t r0 = start + 4 * (w * rpw + k);
+        if (r0 >= m) break;  // warp-uniform
+        const int64_t r = r0 + g;
         float2 acc = make_float2(0.0f, 0.0f);
-        if (vec) {
-            // two chunks in flight per lane, two accumulators
-            const float4* A4 = reinterpret_cast<const float4*>(Ar);
-            const float4* x4 = reinterpret_cast<const float4*>(xv);
-            const int64_t nch = n >> 1;
-            float2 acc1 = make_float2(0.0f, 0.0f);
-            int64_t c = lane;
-            for (; c + 32 < nch; c += 64) {
-                const float4 a0 = __ldcs(A4 + c), a1 = __ldcs(A4 + c + 32);
-                const float4 x0 = __ldg(x4 + c), x1 = __ldg(x4 + c + 32);
-                acc = ffk::add22(acc, ffk::mul22(make_float2(a0.x, a0.y), make_float2(x0.x, x0.y)));
-                acc = ffk::add22(acc, ffk::mul22(make_float2(a0.z, a0.w), make_float2(x0.z, x0.w)));
-                acc1 = ffk::add22(acc1, ffk::mul22(make_float2(a1.x, a1.y), make_float2(x1.x, x1.y)));
-                acc1 = ffk::add22(acc1, ffk::mul22(make_float2(a1.z, a1.w), make_float2(x1.z, x1.w)));
+        if (r < m) {
+            const float2* Ar = A + r * lda;
+            if (vec) {
+                const float4* A4 = reinterpret_cast<const float4*>(Ar);
+                const float4* x4 = reinterpret_cast<const float4*>(xv);
+                const int64_t nch = n >> 1;
+                float2 acc1 = make_float2(0.0f, 0.0f);
+                int64_t c = l8;
+                for (; c + 8 < nch; c += 16) {
+                    const float4 a0 = __ldcs(A4 + c), a1 = __ldcs(A4 + c + 8);
+                    const float4 x0 = __ldg(x4 + c), x1 = __ldg(x4 + c + 8);
+                    acc = ffk::add22(acc, ffk::mul22(make_float2(a0.x, a0.y), make_float2(x0.x, x0.y)));
+                    acc = ffk::add22(acc, ffk::mul22(make_float2(a0.z, a0.w), make_float2(x0.z, x0.w)));
+                    acc1 = ffk::add22(acc1, ffk::mul22(make_float2(a1.x, a1.y), make_float2(x1.x, x1.y)));
+                    acc1 = ffk::add22(acc1, ffk::mul22(make_float2(a1.z, a1.w), make_float2(x1.z, x1.w)));
+                }
+                for (; c < nch; c += 8) {
+                    const float4 a0 = __ldcs(A4 + c);
+                    const float4 x0 = __ldg(x4 + c);
+                    acc = ffk::add22(acc, ffk::mul22(make_float2(a0.x, a0.y), make_float2(x0.x, x0.y)));
+                    acc = ffk::add22(acc, ffk::mul22(make_float2(a0.z, a0.w), make_float2(x0.z, x0.w)));
+                }
+                acc = ffk::add22(acc, acc1);
+                if ((n & 1) && l8 == 0) acc = ffk::add22(acc, ffk::mul22(Ar[n - 1], xv[n - 1]));
+            } else {
+                for (int64_t j = l8; j < n; j += 8) acc = ffk::add22(acc, ffk::mul22(Ar[j], xv[j]));
             }
-            for (; c < nch; c += 32) {
-                const float4 a0 = __ldcs(A4 + c);
-                const float4 x0 = __ldg(x4 + c);
-                acc = ffk::add22(acc, ffk::mul22(make_float2(a0.x, a0.y), make_float2(x0.x, x0.y)));
-                acc = ffk::add22(acc, ffk::mul22(make_float2(a0.z, a0.w), make_float2(x0.z, x0.w)));
-            }
-            acc = ffk::add22(acc, acc1);
-            if ((n & 1) && lane == 0) acc = ffk::add22(acc, ffk::mul22(Ar[n - 1], xv[n - 1]));
-        } else {
-            for (int64_t j = lane; j < n; j += 32) acc = ffk::add22(acc, ffk::mul22(Ar[j], xv[j]));
         }
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) acc = ffk::add22(acc, shfl_down2(acc, off));
-        if (lane == 0) out[r] = acc;
+        for (int off = 4; off > 0; off >>= 1)
+            acc = ffk::add22(acc, make_float2(__shfl_down_sync(0xffffffffu, acc.x, off, 8),
+                                              __shfl_down_sync(0xffffffffu, acc.y, off, 8)));
+        if (l8 == 0 && r < m) out[r] = acc;
     }
 }
 
@@ -464,11 +475,13 @@ ff_status ff_batch_plan_create(const ff_batch_instance* inst, int count, const f
             // rows of 16-byte-aligned storage when the matrix, its row stride
             // and the vector allow it
             d.vec = (ffh::aligned(b.x, 16) && ffh::aligned(b.y, 16) && (b.lda % 2 == 0)) ? 1 : 0;
+            // four rows per warp at a time, rpw groups of four per warp per
+            // tile: about 16K values per tile
             const int64_t warps = tune.block / 32;
-            int64_t rpw = 16384 / (warps * (b.n > 0 ? b.n : 1));
+            int64_t rpw = 16384 / (4 * warps * (b.n > 0 ? b.n : 1));
             rpw = rpw < 1 ? 1 : (rpw > 16 ? 16 : rpw);
             d.rows_per_warp = static_cast<int32_t>(rpw);
-            const int64_t rows_per_tile = warps * rpw;
+            const int64_t rows_per_tile = 4 * warps * rpw;
             const int64_t nt = (b.m + rows_per_tile - 1) / rows_per_tile;
             if (nt > INT32_MAX) return FF_ERR_INVALID_ARG;
             d.ntiles = static_cast<int32_t>(nt);
