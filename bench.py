@@ -757,6 +757,25 @@ def run_case(args):
         dout = torch.tensor([1.0, 0.0], device=dev)
         fn = {"dot": lambda: ff.dot(x, y), "sum": lambda: ff.sum(x),
               "dot_backward": lambda: ff.dot_backward(dout, x, y)}[args.case]
+    elif args.case == "batch_gemv":
+        from paper_cs_0603115_gb300 import batch
+        g = torch.Generator().manual_seed(inputs.seed_for(3, 9))
+        cnt = 256
+        ms = torch.round(2.0 ** (5 + 7 * torch.rand(cnt, generator=g, dtype=torch.float64))).to(torch.int64).tolist()
+        ns = torch.round(2.0 ** (5 + 7 * torch.rand(cnt, generator=g, dtype=torch.float64))).to(torch.int64).tolist()
+        ns = [v + (v & 1) for v in ns]
+        gA = torch.Generator(device=dev).manual_seed(inputs.seed_for(3, 10))
+        Aall = inputs.to_ff(inputs.loguniform_f64(sum(a * b for a, b in zip(ms, ns)), gA, dev))
+        xall = inputs.to_ff(inputs.loguniform_f64(sum(ns), gA, dev))
+        yall = torch.empty((sum(ms), 2), dtype=torch.float32, device=dev)
+        specs, oa, ox, oy = [], 0, 0, 0
+        for mm, nn in zip(ms, ns):
+            specs.append((batch.GEMV, Aall[oa:oa + mm * nn].view(mm, nn, 2), xall[ox:ox + nn], yall[oy:oy + mm], None))
+            oa += mm * nn
+            ox += nn
+            oy += mm
+        plan = batch.BatchPlan(batch.make_instances(specs), tune=(256, 128, 4, 2))
+        fn = plan.run
     elif args.case in ("gemv", "gemv_t"):
         m = int(math.isqrt(n))
         gi = inputs.gemv(m, m, args.k, inputs.seed_for(4, 0), device=dev)
