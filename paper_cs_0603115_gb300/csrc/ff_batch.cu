@@ -68,6 +68,7 @@ struct Tile {
 struct ff_batch_plan {
     int count;
     bool has_gemv_rows;
+    bool only_gemv_rows;
     ff_tune tune;
     int64_t ntiles;
     int64_t ndot;
@@ -118,9 +119,9 @@ __device__ __forceinline__ float2 block_reduce(float2 v, float2* sm)
 // and l + 8 + 16i into its second accumulator (a leftover chunk into the
 // first), adds them, the group combines its eight lanes with a shuffle-down
 // Add22 tree (offsets 4, 2, 1) and its lane 0 writes out[r].  Kept out of
-// line, with its arguments by value.
-__device__ __noinline__ void gemv_rows_tile(const float2* A, const float2* xv, float2* out, int64_t n,
-                                            int64_t lda, int64_t m, int vec, int rpw, int64_t start)
+// line (for the mixed kernel), with its arguments by value.
+__device__ __forceinline__ void gemv_rows_tile_body(const float2* A, const float2* xv, float2* out, int64_t n,
+                                                   int64_t lda, int64_t m, int vec, int rpw, int64_t start)
 {
     const int lane = threadIdx.x & 31;
     const int g = lane >> 3;
@@ -165,6 +166,12 @@ __device__ __noinline__ void gemv_rows_tile(const float2* A, const float2* xv, f
                                               __shfl_down_sync(0xffffffffu, acc.y, off, 8)));
         if (l8 == 0 && r < m) out[r] = acc;
     }
+}
+
+__device__ __noinline__ void gemv_rows_tile(const float2* A, const float2* xv, float2* out, int64_t n,
+                                            int64_t lda, int64_t m, int vec, int rpw, int64_t start)
+{
+    gemv_rows_tile_body(A, xv, out, n, lda, m, vec, rpw, start);
 }
 
 // PPT values per thread per tile (even).  Values of a tile are visited as
@@ -345,17 +352,33 @@ batch_kernel(const DevInst* __restrict__ insts, const Tile* __restrict__ tiles, 
     }
 }
 
+// Kernel for plans whose records are all GEMV rows: the same tile walk and
+// row reduction, without the other paths, so that it needs few registers and
+// keeps many warps resident (the rows are latency-bound).
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK)
+batch_gemv_kernel(const DevInst* __restrict__ insts, const Tile* __restrict__ tiles, int64_t ntiles,
+                  float2* __restrict__, unsigned* __restrict__)
+{
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const Tile tl = tiles[t];
+        const DevInst& I = insts[tl.inst];
+        gemv_rows_tile_body(I.x, I.y, I.out, I.n, I.lda, I.m, I.vec, I.rows_per_warp, tl.start);
+    }
+}
+
 using KernelFn = void (*)(const DevInst*, const Tile*, int64_t, float2*, unsigned*);
 
 struct Variant {
     int block;
     int ppt;
     int unroll;
-    KernelFn fn;        // plans without GEMV rows
-    KernelFn fn_gemv;   // plans with GEMV rows
+    KernelFn fn;            // plans without GEMV rows
+    KernelFn fn_gemv;       // plans with GEMV rows and other records
+    KernelFn fn_gemv_only;  // plans whose records are all GEMV rows
 };
 
-#define FF_BV(B, P, UN) {B, P, UN, batch_kernel<B, P, UN, false>, batch_kernel<B, P, UN, true>}
+#define FF_BV(B, P, UN) {B, P, UN, batch_kernel<B, P, UN, false>, batch_kernel<B, P, UN, true>, batch_gemv_kernel<B>}
 #define FF_BATCH_VARIANTS(UN)                                                                              \
     FF_BV(128, 16, UN), FF_BV(128, 32, UN), FF_BV(128, 64, UN), FF_BV(128, 128, UN), FF_BV(256, 8, UN),        \
         FF_BV(256, 16, UN), FF_BV(256, 32, UN), FF_BV(256, 64, UN), FF_BV(256, 128, UN), FF_BV(512, 8, UN),    \
@@ -374,6 +397,11 @@ const Variant* find_variant(const ff_tune& t)
 }
 
 const ff_tune kDefaultTune = {256, 32, 0, 4};
+
+KernelFn kernel_for(const Variant& v, const ff_batch_plan& p)
+{
+    return p.only_gemv_rows ? v.fn_gemv_only : (p.has_gemv_rows ? v.fn_gemv : v.fn);
+}
 
 size_t ws_bytes_for(const ff_batch_plan* p)
 {
@@ -504,7 +532,11 @@ ff_status ff_batch_plan_create(const ff_batch_instance* inst, int count, const f
     if (!p) return FF_ERR_UNSUPPORTED;
     p->count = static_cast<int>(recs.size());
     p->has_gemv_rows = false;
-    for (const Rec& r : recs) p->has_gemv_rows |= (r.kind == kGemvRows);
+    p->only_gemv_rows = !recs.empty();
+    for (const Rec& r : recs) {
+        p->has_gemv_rows |= (r.kind == kGemvRows);
+        p->only_gemv_rows &= (r.kind == kGemvRows);
+    }
     p->tune = tune;
     p->ntiles = static_cast<int64_t>(ht.size());
     p->ndot = ndot;
@@ -512,7 +544,7 @@ ff_status ff_batch_plan_create(const ff_batch_instance* inst, int count, const f
     p->device = di.device;
     int bps = tune.blocks_per_sm;
     if (bps == 0)
-        bps = ffh::occupancy(reinterpret_cast<const void*>(p->has_gemv_rows ? var->fn_gemv : var->fn), tune.block);
+        bps = ffh::occupancy(reinterpret_cast<const void*>(kernel_for(*var, *p)), tune.block);
     int64_t grid = static_cast<int64_t>(di.sm_count) * (bps > 0 ? bps : 1);
     if (grid > p->ntiles) grid = p->ntiles > 0 ? p->ntiles : 1;
     p->grid = static_cast<unsigned>(grid);
@@ -560,8 +592,7 @@ ff_status ff_batch_run(const ff_batch_plan* p, void* ws, size_t ws_bytes, cudaSt
     auto* partials = reinterpret_cast<float2*>(static_cast<char*>(ws) + cbytes);
     ff_status st = ffh::cuda_status(cudaMemsetAsync(counters, 0, static_cast<size_t>(p->count) * 4, s));
     if (st != FF_OK) return st;
-    KernelFn fn = p->has_gemv_rows ? var->fn_gemv : var->fn;
-    fn<<<p->grid, p->tune.block, 0, s>>>(p->d_inst, p->d_tiles, p->ntiles, partials, counters);
+    kernel_for(*var, *p)<<<p->grid, p->tune.block, 0, s>>>(p->d_inst, p->d_tiles, p->ntiles, partials, counters);
     return ffh::check_launch();
 }
 
