@@ -252,8 +252,8 @@ def run_gpu(args):
     import paper_cs_0603115_gb300 as ff
     from paper_cs_0603115_gb300 import build as ffbuild
     from paper_cs_0603115_gb300 import inputs
-    if rank == 0 or not os.path.exists(ffbuild.LIB_PATH):
-        ffbuild.build()
+    if rank == 0:
+        ffbuild.build()     # one rank builds; the others wait and load it
     barrier(dist)
     lib = ff.load()
     build_id = lib.ff_build_id().decode()

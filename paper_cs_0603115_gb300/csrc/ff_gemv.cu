@@ -260,24 +260,27 @@ __global__ void __launch_bounds__(kGBlock)
 gemv_dA_kernel(const float2* __restrict__ dY, int64_t m, int64_t lddy, const float2* __restrict__ X, int64_t n,
                int64_t ldx, int64_t k, float2* __restrict__ dA, int64_t ldda)
 {
-    const int64_t r = blockIdx.y;
-    if (VEC) {
-        const int64_t jp = static_cast<int64_t>(blockIdx.x) * kGBlock + threadIdx.x;
-        if (2 * jp >= n) return;
-        float2 acc0 = make_float2(0.0f, 0.0f), acc1 = make_float2(0.0f, 0.0f);
-        for (int64_t c = 0; c < k; ++c) {
-            const float2 d = __ldg(dY + c * lddy + r);
-            const float4 x = __ldg(reinterpret_cast<const float4*>(X + c * ldx) + jp);
-            acc0 = ffk::add22(acc0, ffk::mul22(d, make_float2(x.x, x.y)));
-            acc1 = ffk::add22(acc1, ffk::mul22(d, make_float2(x.z, x.w)));
+    // rows r = blockIdx.y, blockIdx.y + gridDim.y, ... (gridDim.y <= 65535)
+    for (int64_t r = blockIdx.y; r < m; r += gridDim.y) {
+        if (VEC) {
+            const int64_t jp = static_cast<int64_t>(blockIdx.x) * kGBlock + threadIdx.x;
+            if (2 * jp >= n) return;
+            float2 acc0 = make_float2(0.0f, 0.0f), acc1 = make_float2(0.0f, 0.0f);
+            for (int64_t c = 0; c < k; ++c) {
+                const float2 d = __ldg(dY + c * lddy + r);
+                const float4 x = __ldg(reinterpret_cast<const float4*>(X + c * ldx) + jp);
+                acc0 = ffk::add22(acc0, ffk::mul22(d, make_float2(x.x, x.y)));
+                acc1 = ffk::add22(acc1, ffk::mul22(d, make_float2(x.z, x.w)));
+            }
+            __stcs(reinterpret_cast<float4*>(dA + r * ldda) + jp, make_float4(acc0.x, acc0.y, acc1.x, acc1.y));
+        } else {
+            const int64_t j = static_cast<int64_t>(blockIdx.x) * kGBlock + threadIdx.x;
+            if (j >= n) return;
+            float2 acc = make_float2(0.0f, 0.0f);
+            for (int64_t c = 0; c < k; ++c)
+                acc = ffk::add22(acc, ffk::mul22(__ldg(dY + c * lddy + r), X[c * ldx + j]));
+            dA[r * ldda + j] = acc;
         }
-        __stcs(reinterpret_cast<float4*>(dA + r * ldda) + jp, make_float4(acc0.x, acc0.y, acc1.x, acc1.y));
-    } else {
-        const int64_t j = static_cast<int64_t>(blockIdx.x) * kGBlock + threadIdx.x;
-        if (j >= n) return;
-        float2 acc = make_float2(0.0f, 0.0f);
-        for (int64_t c = 0; c < k; ++c) acc = ffk::add22(acc, ffk::mul22(__ldg(dY + c * lddy + r), X[c * ldx + j]));
-        dA[r * ldda + j] = acc;
     }
 }
 
@@ -422,7 +425,6 @@ ff_status ff_gemv_dA(const ff2* dY_, int64_t m, int64_t lddy, const ff2* X_, int
                      ff2* dA_, int64_t ldda, cudaStream_t s)
 {
     if (bad_dims(m, n, k) || lddy < m || ldx < n || ldda < n) return FF_ERR_INVALID_ARG;
-    if (m > 2147483647) return FF_ERR_INVALID_ARG;  // one grid row per row of dA
     const size_t an = static_cast<size_t>(m) * static_cast<size_t>(n);
     if (!ffh::ok_ptr(dY_, static_cast<size_t>(m)) || !ffh::ok_ptr(X_, static_cast<size_t>(n)) || !ffh::ok_ptr(dA_, an))
         return FF_ERR_INVALID_ARG;
@@ -431,11 +433,12 @@ ff_status ff_gemv_dA(const ff2* dY_, int64_t m, int64_t lddy, const ff2* X_, int
     auto* X = reinterpret_cast<const float2*>(X_);
     auto* dA = reinterpret_cast<float2*>(dA_);
     const bool vec = (n % 2 == 0) && (ldx % 2 == 0) && (ldda % 2 == 0) && ffh::aligned(X, 16) && ffh::aligned(dA, 16);
+    const unsigned gy = static_cast<unsigned>(m < 65535 ? m : 65535);
     if (vec) {
-        dim3 grid(static_cast<unsigned>((n / 2 + kGBlock - 1) / kGBlock), static_cast<unsigned>(m));
+        dim3 grid(static_cast<unsigned>((n / 2 + kGBlock - 1) / kGBlock), gy);
         gemv_dA_kernel<true><<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, k, dA, ldda);
     } else {
-        dim3 grid(static_cast<unsigned>((n + kGBlock - 1) / kGBlock), static_cast<unsigned>(m));
+        dim3 grid(static_cast<unsigned>((n + kGBlock - 1) / kGBlock), gy);
         gemv_dA_kernel<false><<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, k, dA, ldda);
     }
     return ffh::check_launch();

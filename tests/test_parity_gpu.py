@@ -355,3 +355,69 @@ def test_more_than_2_32_values_elementwise_and_dot():
     assert r[0] == hi and float(r[1]) == float(n - float(hi))
     del a
     torch.cuda.empty_cache()
+
+
+# ---------------------------------------------------------------------------
+# guard regions: no kernel writes outside its output
+# ---------------------------------------------------------------------------
+GUARD = 64
+SENTINEL = np.array([0x7FC0DEAD], dtype=np.uint32).view(np.float32)[0]
+
+
+def guarded(rows, offset=0, width=2):
+    """A view of `rows` float32 rows inside a buffer with GUARD sentinel rows
+    on both sides (the view starts `offset` rows past the guard)."""
+    buf = torch.full((rows + 2 * GUARD + offset, width), float(SENTINEL), dtype=torch.float32, device=DEV)
+    view = buf[GUARD + offset:GUARD + offset + rows]
+    return buf, view
+
+
+def guards_intact(buf, rows, offset=0):
+    b = buf.cpu().numpy().view(np.uint32)
+    s = np.array([0x7FC0DEAD], np.uint32)[0]
+    return bool((b[:GUARD + offset] == s).all() and (b[GUARD + offset + rows:] == s).all())
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 4099, 65537])
+@pytest.mark.parametrize("offset", [0, 1])
+def test_outputs_stay_inside_their_bounds(cfg0, n, offset):
+    a = gpu(cfg0.a[:n])
+    b = gpu(cfg0.b[:n])
+    for name, fn in (("add", lambda o: ff.add(a, b, out=o)), ("mul", lambda o: ff.mul(a, b, out=o)),
+                     ("div", lambda o: ff.div(a, b, out=o)), ("sqrt", lambda o: ff.sqrt(a.abs(), out=o)),
+                     ("add_accurate", lambda o: ff.add_accurate(a, b, out=o)),
+                     ("add12", lambda o: ff.add12(gpu(cfg0.ab[:n]), out=o)),
+                     ("mul12", lambda o: ff.mul12(gpu(cfg0.ab[:n]), out=o)),
+                     ("axpy", lambda o: ff.axpy((1.5, 0.0), a, b, out=o))):
+        buf, view = guarded(n, offset)
+        fn(view)
+        torch.cuda.synchronize()
+        assert guards_intact(buf, n, offset), name
+    bx, dx = guarded(n, offset)
+    by, dy = guarded(n, offset)
+    ff.dot_backward(gpu(torch.tensor([1.25, 0.0])), a, b, dx, dy)
+    torch.cuda.synchronize()
+    assert guards_intact(bx, n, offset) and guards_intact(by, n, offset)
+    br, r = guarded(1, offset)
+    ff.dot(a, b, out=r.reshape(2))
+    ff.sum(a, out=r.reshape(2))
+    torch.cuda.synchronize()
+    assert guards_intact(br, 1, offset)
+
+
+@pytest.mark.parametrize("m,n,k", [(9, 7, 1), (33, 130, 5), (70, 64, 17)])
+def test_gemv_outputs_stay_inside_their_bounds(m, n, k):
+    gi = inputs.gemv(m, n, k, inputs.seed_for(4, 90 + k))
+    A, X, dY = gpu(gi.A), gpu(gi.X), gpu(gi.dY)
+    buf, view = guarded(k * m)
+    ff.gemv(A, X, out=view.view(k, m, 2))
+    torch.cuda.synchronize()
+    assert guards_intact(buf, k * m)
+    buf, view = guarded(k * n)
+    ff.gemv_t(A, dY, out=view.view(k, n, 2))
+    torch.cuda.synchronize()
+    assert guards_intact(buf, k * n)
+    buf, view = guarded(m * n)
+    ff.gemv_dA(dY, X, out=view.view(m, n, 2))
+    torch.cuda.synchronize()
+    assert guards_intact(buf, m * n)
