@@ -1,0 +1,82 @@
+"""Sharded float-float reductions over several GPUs (one process per GPU).
+
+A dot product or sum sharded over ranks has one real exchange step: every
+rank reduces its contiguous shard with the library's kernel, the ranks
+all-gather their 8-byte float-float partials, and every rank combines the
+gathered partials in rank order with Add22 (the library's ff_sum on the
+rank-ordered vector of partials), so all ranks hold the same bits.  A
+collective sum (e.g. NCCL's SUM) cannot be used: it would add the high and
+the low parts separately.
+
+GEMV needs no exchange when A is sharded by rows (each rank owns its rows of
+Y); its adjoint dX = A^T dY does: every rank computes the (n, k) partial of
+its rows, the partials are all-gathered and added in rank order with Add22
+(ff_add, one launch per rank after the first).
+
+The compute functions are arguments (defaulting to the library's kernels)
+so that the exchange logic can be exercised on CPU-only ranks with stand-ins.
+"""
+from __future__ import annotations
+
+import torch
+
+
+def shard_range(n: int, rank: int, world: int) -> tuple[int, int]:
+    """Contiguous shard [lo, hi) of n items for `rank` of `world` (the first
+    n % world ranks get one more item)."""
+    base, extra = divmod(n, world)
+    lo = rank * base + min(rank, extra)
+    hi = lo + base + (1 if rank < extra else 0)
+    return lo, hi
+
+
+def _all_gather_rows(t: torch.Tensor, group=None) -> torch.Tensor:
+    """(world, *t.shape): every rank's tensor, in rank order."""
+    import torch.distributed as dist
+    world = dist.get_world_size(group)
+    parts = [torch.empty_like(t) for _ in range(world)]
+    dist.all_gather(parts, t.contiguous(), group=group)
+    return torch.stack(parts)
+
+
+def combine_partials(parts: torch.Tensor, sum_fn=None) -> torch.Tensor:
+    """Rank-ordered Add22 combination of (world, 2) float-float partials."""
+    if sum_fn is None:
+        from . import sum as sum_fn
+    return sum_fn(parts.contiguous())
+
+
+def sharded_dot(x_local: torch.Tensor, y_local: torch.Tensor, group=None, dot_fn=None, sum_fn=None):
+    """Float-float dot product of vectors sharded over the ranks of `group`
+    (each rank passes its own contiguous shard).  Returns the (2,) result,
+    bit-identical on every rank."""
+    if dot_fn is None:
+        from . import dot as dot_fn
+    local = dot_fn(x_local, y_local)
+    parts = _all_gather_rows(local.reshape(2), group)
+    return combine_partials(parts, sum_fn)
+
+
+def sharded_sum(x_local: torch.Tensor, group=None, sum_fn=None):
+    """Float-float sum of a vector sharded over the ranks of `group`."""
+    if sum_fn is None:
+        from . import sum as sum_fn
+    local = sum_fn(x_local)
+    parts = _all_gather_rows(local.reshape(2), group)
+    return combine_partials(parts, sum_fn)
+
+
+def sharded_gemv_t(A_local: torch.Tensor, dY_local: torch.Tensor, group=None, gemv_t_fn=None, add_fn=None):
+    """dX = A^T dY for A sharded by rows: A_local (m_r, n, 2) and dY_local
+    (k, m_r, 2) are this rank's rows.  Returns the (k, n, 2) dX, equal on every
+    rank: the per-rank partials are added in rank order with Add22."""
+    if gemv_t_fn is None:
+        from . import gemv_t as gemv_t_fn
+    if add_fn is None:
+        from . import add as add_fn
+    local = gemv_t_fn(A_local, dY_local)
+    parts = _all_gather_rows(local, group)
+    acc = parts[0].contiguous()
+    for r in range(1, parts.shape[0]):
+        acc = add_fn(acc, parts[r].contiguous())
+    return acc

@@ -42,3 +42,79 @@ def test_two_rank_timing_aggregation():
         assert p.exitcode == 0
     assert [r[1] for r in res] == [1.5, 1.5]
     assert all(abs(r[2] - 2 * (6 << 28) * 10 / 1.5) < 1e-3 for r in res)
+
+
+def _shard_worker(rank, world, port, q):
+    """Sharded dot, sum and GEMV adjoint on two CPU ranks, with the oracle as
+    the stand-in for the per-rank kernels (the exchange logic is what is
+    under test)."""
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    import oracle
+    from paper_cs_0603115_gb300 import dist as ffdist
+    from paper_cs_0603115_gb300 import inputs
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    n = 10007
+    g = inputs.ill_dot(n, 1e9, 4242)
+    lo, hi = ffdist.shard_range(n, rank, world)
+    dot_fn = lambda x, y: torch.from_numpy(oracle.ff_dot(x.numpy(), y.numpy()))
+    sum_fn = lambda v: torch.from_numpy(oracle.ff_sum(v.numpy()))
+    d = ffdist.sharded_dot(g.x[lo:hi], g.y[lo:hi], dot_fn=dot_fn, sum_fn=sum_fn)
+    s = ffdist.sharded_sum(g.x[lo:hi], sum_fn=sum_fn)
+    gi = inputs.gemv(12, 9, 3, 77)
+    r0, r1 = ffdist.shard_range(12, rank, world)
+    gt_fn = lambda A, dY: torch.from_numpy(oracle.gemv_t(A.numpy(), dY.numpy()))
+    add_fn = lambda a, b: torch.from_numpy(oracle.add22(a.numpy().reshape(-1, 2), b.numpy().reshape(-1, 2)).reshape(a.shape))
+    dX = ffdist.sharded_gemv_t(gi.A[r0:r1].contiguous(), gi.dY[:, r0:r1].contiguous(), gemv_t_fn=gt_fn, add_fn=add_fn)
+    q.put((rank, d.numpy().tobytes(), s.numpy().tobytes(), dX.numpy().tobytes()))
+    dist.destroy_process_group()
+
+
+def test_sharded_reductions_two_ranks():
+    import numpy as np
+    import oracle
+    from paper_cs_0603115_gb300 import dist as ffdist
+    from paper_cs_0603115_gb300 import inputs
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_shard_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=180) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    # every rank holds the same bits
+    assert res[0][1:] == res[1][1:]
+    # and they are the rank-ordered combination of the per-shard results
+    n = 10007
+    g = inputs.ill_dot(n, 1e9, 4242)
+    x, y = g.x.numpy(), g.y.numpy()
+    parts = []
+    for r in range(2):
+        lo, hi = ffdist.shard_range(n, r, 2)
+        parts.append(oracle.ff_dot(x[lo:hi], y[lo:hi]))
+    want = oracle.ff_sum(np.stack(parts))
+    got = np.frombuffer(res[0][1], np.float32)
+    assert np.array_equal(got, want)
+    _, _, A, E = oracle.exact_dot(x, y, got)
+    assert abs(E) <= n * 2.0 ** -46 * A
+    gi = inputs.gemv(12, 9, 3, 77)
+    dX = np.frombuffer(res[0][3], np.float32).reshape(3, 9, 2)
+    p0 = oracle.gemv_t(gi.A[:6].numpy(), gi.dY[:, :6].numpy())
+    p1 = oracle.gemv_t(gi.A[6:].numpy(), gi.dY[:, 6:].numpy())
+    np.testing.assert_array_equal(dX, oracle.add22(p0.reshape(-1, 2), p1.reshape(-1, 2)).reshape(3, 9, 2))
+
+
+def test_shard_ranges_cover_exactly():
+    from paper_cs_0603115_gb300 import dist as ffdist
+    for n in (0, 1, 7, 10007):
+        for w in (1, 2, 3, 8):
+            spans = [ffdist.shard_range(n, r, w) for r in range(w)]
+            assert spans[0][0] == 0 and spans[-1][1] == n
+            assert all(a[1] == b[0] for a, b in zip(spans, spans[1:]))
+            assert max(h - l for l, h in spans) - min(h - l for l, h in spans) <= 1
