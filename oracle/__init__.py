@@ -90,6 +90,7 @@ def _declare(L: ctypes.CDLL) -> None:
         "orc_gemv": [P, I64, I64, I64, P, I64, I64, P, I64],
         "orc_gemv_t": [P, I64, I64, I64, P, I64, I64, P, I64],
         "orc_gemv_dA": [P, I64, I64, P, I64, I64, I64, P, I64],
+        "orc_gemm": [ctypes.c_int, ctypes.c_int, I64, I64, I64, P, I64, P, I64, P, I64],
         "orc_fp32_add": [P, P, P, S], "orc_fp32_mul": [P, P, P, S],
         "orc_fp32_mad": [P, P, P, P, S],
         "exact_sum_f64_q": [P, S, P], "exact_count_sum2_mismatch": [P, P, S],
@@ -235,6 +236,19 @@ def gemv_t(A, dY):
     k = dY.shape[0]
     dX = np.empty((k, n, 2), np.float32)
     lib().orc_gemv_t(_p(A), m, n, n, _p(dY), m, k, _p(dX), n); return dX
+
+
+def gemm(A, B, transa=False, transb=False):
+    """C = op(A) op(B), float-float, accumulated in order of the inner index.
+    A: (m, kk, 2), or (kk, m, 2) when transa; B: (kk, n, 2), or (n, kk, 2)
+    when transb.  Returns C as (m, n, 2)."""
+    A = _f32(A); B = _f32(B)
+    kk, m = (A.shape[0], A.shape[1]) if transa else (A.shape[1], A.shape[0])
+    n = B.shape[0] if transb else B.shape[1]
+    assert (B.shape[1] if transb else B.shape[0]) == kk
+    C = np.empty((m, n, 2), np.float32)
+    lib().orc_gemm(int(transa), int(transb), m, n, kk, _p(A), A.shape[1], _p(B), B.shape[1], _p(C), n)
+    return C
 
 
 def gemv_dA(dY, X):

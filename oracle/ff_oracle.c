@@ -33,8 +33,8 @@
  *   - Div22 and Sqrt22 are not in the paper; they follow Dekker's div2 and
  *     sqrt2 (Dekker 1971, the paper's reference for Split and Mul12) with the
  *     paper's Add12 as the final renormalisation.
- *   - Reductions (sum, dot), AXPY, GEMV and the dot backward are not in the
- *     paper either; they are the plain left-to-right Add22 accumulation of
+ *   - Reductions (sum, dot), AXPY, GEMV, GEMM and the dot backward are not
+ *     in the paper either; they are the plain left-to-right Add22 accumulation of
  *     the paper's operators (the compensated algorithms Section 7 names as
  *     future work).
  */
@@ -198,6 +198,31 @@ void orc_gemv_dA(const float *dY, int64_t m, int64_t lddy, const float *X, int64
             }
             dA[2 * (r * ldda + j)] = h;
             dA[2 * (r * ldda + j) + 1] = l;
+        }
+    }
+}
+
+/* Float-float matrix product C = op(A) op(B) (a GEMV with many right-hand
+ * sides; not in the paper), all matrices row-major:
+ *   C[i, j] = acc over p = 0 .. kk-1 of Add22(acc, Mul22(op(A)[i, p], op(B)[p, j])),
+ * acc starting at (0, 0), p in increasing order.  op(A)[i, p] is A[i, p]
+ * (A is m x kk, leading dimension lda) or, when transa, A[p, i] (A is kk x m);
+ * op(B)[p, j] is B[p, j] (kk x n, ldb) or, when transb, B[j, p] (n x kk). */
+void orc_gemm(int transa, int transb, int64_t m, int64_t n, int64_t kk,
+              const float *A, int64_t lda, const float *B, int64_t ldb, float *C, int64_t ldc)
+{
+    for (int64_t i = 0; i < m; ++i) {
+        for (int64_t j = 0; j < n; ++j) {
+            float h = 0.0f, l = 0.0f;
+            for (int64_t p = 0; p < kk; ++p) {
+                const float *a = transa ? &A[2 * (p * lda + i)] : &A[2 * (i * lda + p)];
+                const float *b = transb ? &B[2 * (j * ldb + p)] : &B[2 * (p * ldb + j)];
+                float ph, pl;
+                mul22(a[0], a[1], b[0], b[1], &ph, &pl);
+                add22(h, l, ph, pl, &h, &l);
+            }
+            C[2 * (i * ldc + j)] = h;
+            C[2 * (i * ldc + j) + 1] = l;
         }
     }
 }

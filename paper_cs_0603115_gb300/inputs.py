@@ -252,6 +252,23 @@ def gemv(m: int, n: int, k: int, seed: int, device="cpu") -> GemvInputs:
     return GemvInputs(A=A, X=X, dY=dY)
 
 
+@dataclass
+class GemmInputs:
+    A: torch.Tensor   # (m, kk, 2)
+    B: torch.Tensor   # (kk, n, 2)
+    dC: torch.Tensor  # (m, n, 2)
+
+
+def gemm(m: int, n: int, kk: int, seed: int, device="cpu") -> GemmInputs:
+    """Row-major A (m x kk), B (kk x n) and an output gradient dC (m x n), all
+    with the elementwise magnitude law (no forced cancellation)."""
+    g = _gen(seed, device)
+    A = to_ff(loguniform_f64(m * kk, g, device)).reshape(m, kk, 2)
+    B = to_ff(loguniform_f64(kk * n, g, device)).reshape(kk, n, 2)
+    dC = to_ff(loguniform_f64(m * n, g, device)).reshape(m, n, 2)
+    return GemmInputs(A=A, B=B, dC=dC)
+
+
 def batch_lengths(count: int, seed: int, lo_exp: float = 2.0, hi_exp: float = 7.0):
     """Instance lengths round(10^(lo + (hi - lo) u)), u uniform, and kinds: half
     dot (0), half AXPY (1), assigned by a seeded shuffle."""

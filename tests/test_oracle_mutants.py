@@ -51,6 +51,8 @@ MUTANTS = [
     ("fast2sum: sign", "    float t = b - z;", "    float t = z - b;"),
     ("sum2: error term dropped", "        add12(p, x[i], &p, &q);\n        s = s + q;", "        add12(p, x[i], &p, &q);\n        s = s + 0.0f * q;"),
     ("dot2: product error r dropped", "        s = s + (q + r);", "        s = s + q;"),
+    ("gemm: op(A) index not transposed", "transa ? &A[2 * (p * lda + i)]", "transa ? &A[2 * (i * lda + p)]"),
+    ("gemm: B read by column", ": &B[2 * (p * ldb + j)];", ": &B[2 * (j * ldb + p)];"),
 ]
 
 # quick pins first; each mutant stops at the first pin that fails
@@ -71,6 +73,7 @@ PINS = [
     (pins.test_dot2_reduces_to_sum2_and_twoproduct, ()), (pins.test_add22_reduces_to_add12, ()),
     (pins.test_mul22_reduces_to_mul12, ()), (pins.test_mul12_bruteforce_exact_and_forms_agree, ()),
     (pins.test_dot_ill_conditioned_within_bound, (1e12,)),
+    (pins.test_gemm_small_integers_exact, ()), (pins.test_gemm_within_bound_and_transpose_identity, ()),
 ]
 
 

@@ -593,3 +593,63 @@ def test_gemv_dA_outer_product_and_bound(orc):
         for j in range(n):
             _, _, Aabs, E = orc.exact_dot(np.ascontiguousarray(dY[:, r]), np.ascontiguousarray(X[:, j]), dA[r, j])
             assert abs(E) <= k * 2.0 ** -44 * Aabs
+
+
+# --------------------------------------------------------------------------
+# GEMM (many right-hand sides; Mul22 products, Add22 accumulation)
+# --------------------------------------------------------------------------
+
+def test_gemm_small_integers_exact(orc):
+    """Integer matrices whose products and partial sums stay below 2^24 are
+    multiplied exactly: the float-float result equals the integer product
+    (numpy int64), for non-square shapes and every transpose combination."""
+    rng = np.random.default_rng(11)
+    m, n, kk = 5, 7, 9
+    Ai = rng.integers(-300, 300, size=(m, kk))
+    Bi = rng.integers(-300, 300, size=(kk, n))
+    want = Ai @ Bi
+    A = np.zeros((m, kk, 2), np.float32); A[..., 0] = Ai
+    B = np.zeros((kk, n, 2), np.float32); B[..., 0] = Bi
+    At = np.ascontiguousarray(A.transpose(1, 0, 2))
+    Bt = np.ascontiguousarray(B.transpose(1, 0, 2))
+    for ta, tb in ((0, 0), (1, 0), (0, 1), (1, 1)):
+        C = orc.gemm(At if ta else A, Bt if tb else B, transa=bool(ta), transb=bool(tb))
+        np.testing.assert_array_equal(C[..., 0].astype(np.int64), want)
+        assert np.all(C[..., 1] == 0)
+
+
+def test_gemm_identity_and_unit_columns(orc):
+    gi = inputs.gemm(6, 11, 8, inputs.seed_for(4, 60))
+    A, B = gi.A.numpy(), gi.B.numpy()
+    I8 = np.zeros((8, 8, 2), np.float32); I8[np.arange(8), np.arange(8), 0] = 1.0
+    I6 = np.zeros((6, 6, 2), np.float32); I6[np.arange(6), np.arange(6), 0] = 1.0
+    np.testing.assert_array_equal(orc.gemm(A, I8), orc.add12(A.reshape(-1, 2)).reshape(A.shape))
+    np.testing.assert_array_equal(orc.gemm(I8, B), orc.add12(B.reshape(-1, 2)).reshape(B.shape))
+    np.testing.assert_array_equal(orc.gemm(I6, A), orc.add12(A.reshape(-1, 2)).reshape(A.shape))
+    # a unit column of B picks out one column of A
+    E = np.zeros((8, 1, 2), np.float32); E[3, 0, 0] = 1.0
+    np.testing.assert_array_equal(orc.gemm(A, E)[:, 0], orc.add12(A[:, 3]))
+
+
+def test_gemm_within_bound_and_transpose_identity(orc):
+    """Every element within kk 2^-44 sum|a b| of the exact value (the
+    superaccumulator); C^T = B^T A^T bit for bit (Mul22 with a fused Mul12
+    is symmetric in its operands and the accumulation order is the same)."""
+    m, n, kk = 7, 5, 133
+    gi = inputs.gemm(m, n, kk, inputs.seed_for(4, 61))
+    A, B = gi.A.numpy(), gi.B.numpy()
+    C = orc.gemm(A, B)
+    for i in range(m):
+        for j in range(n):
+            _, _, Aabs, Err = orc.exact_dot(A[i], np.ascontiguousarray(B[:, j]), C[i, j])
+            assert abs(Err) <= kk * 2.0 ** -44 * Aabs
+    Ct = orc.gemm(B, A, transa=True, transb=True)
+    np.testing.assert_array_equal(Ct, np.ascontiguousarray(C.transpose(1, 0, 2)))
+    # one row times one column is the float-float dot of the two
+    np.testing.assert_array_equal(orc.gemm(A[2:3], B[:, 4:5])[0, 0], orc.ff_dot(A[2], np.ascontiguousarray(B[:, 4])))
+
+
+def test_gemm_empty_inner_dimension(orc):
+    A = np.zeros((3, 0, 2), np.float32); B = np.zeros((0, 4, 2), np.float32)
+    C = orc.gemm(A, B)
+    assert C.shape == (3, 4, 2) and np.all(bits(C) == 0)
