@@ -178,18 +178,32 @@ def time_fn(torch, fn, reps: int, warm: int = 2) -> float:
     return ev0.elapsed_time(ev1) / 1e3 / reps
 
 
-def cpu_baseline(e_gpu, min_seconds: float = 10.0):
-    """The CPU oracle as it stands (single-threaded C) on the first 2^26
-    values of the same arrays, repeated until at least min_seconds."""
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_ops(a, b, ab, asq, threads: int):
+    """The six elementwise operators of the oracle over the given arrays, each
+    split into `threads` contiguous chunks run on that many host threads (the
+    oracle's C loops release the GIL; the oracle itself is unchanged)."""
+    import concurrent.futures as cf
     import oracle
-    n = 1 << 26
-    a = e_gpu.a[:n].cpu().numpy()
-    b = e_gpu.b[:n].cpu().numpy()
-    ab = e_gpu.ab[:n].cpu().numpy()
-    asq = e_gpu.a_sqrt[:n].cpu().numpy()
     oracle.lib()
-    fns = [lambda: oracle.add12(ab), lambda: oracle.mul12(ab), lambda: oracle.add22(a, b),
-           lambda: oracle.mul22(a, b), lambda: oracle.div22(a, b), lambda: oracle.sqrt22(asq)]
+    n = a.shape[0]
+    cuts = [n * i // threads for i in range(threads + 1)]
+    ch = [slice(cuts[i], cuts[i + 1]) for i in range(threads)]
+    ops = [lambda s: oracle.add12(ab[s]), lambda s: oracle.mul12(ab[s]), lambda s: oracle.add22(a[s], b[s]),
+           lambda s: oracle.mul22(a[s], b[s]), lambda s: oracle.div22(a[s], b[s]), lambda s: oracle.sqrt22(asq[s])]
+    if threads == 1:
+        return [lambda f=f: f(slice(0, n)) for f in ops], None
+    pool = cf.ThreadPoolExecutor(max_workers=threads)
+    return [lambda f=f: list(pool.map(f, ch)) for f in ops], pool
+
+
+def _time_oracle(fns, min_seconds):
     t0 = time.perf_counter()
     reps = 0
     while True:
@@ -198,10 +212,33 @@ def cpu_baseline(e_gpu, min_seconds: float = 10.0):
         reps += 1
         if time.perf_counter() - t0 >= min_seconds:
             break
-    dt = time.perf_counter() - t0
-    return {"value": reps * len(fns) * n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"first 2^26 values of the same arrays, all six operators, {reps} pass(es), "
-                      f"{dt:.1f} s, single-threaded C oracle"}
+    return reps, time.perf_counter() - t0
+
+
+def cpu_baseline(e_gpu, min_seconds: float = 8.0):
+    """The CPU oracle as it stands on the first 2^26 values of the same
+    arrays, repeated until at least min_seconds: on one host core, then on all
+    of them (contiguous chunks, one per core)."""
+    n = 1 << 26
+    a = e_gpu.a[:n].cpu().numpy()
+    b = e_gpu.b[:n].cpu().numpy()
+    ab = e_gpu.ab[:n].cpu().numpy()
+    asq = e_gpu.a_sqrt[:n].cpu().numpy()
+    fns1, _ = oracle_ops(a, b, ab, asq, 1)
+    reps1, dt1 = _time_oracle(fns1, min_seconds)
+    cores = host_cores()
+    fnsT, pool = oracle_ops(a, b, ab, asq, cores)
+    if pool is not None:
+        for f in fnsT:
+            f()
+    repsT, dtT = _time_oracle(fnsT, min_seconds)
+    if pool is not None:
+        pool.shutdown()
+    single = reps1 * 6 * n / dt1
+    return {"value": repsT * 6 * n / dtT, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "single_core_value": single,
+            "sample": f"first 2^26 values of the same arrays, all six operators: {repsT} pass(es) in {dtT:.1f} s "
+                      f"on {cores} host threads (contiguous chunks); {reps1} pass(es) in {dt1:.1f} s on one"}
 
 
 # sources that define the elementwise kernels (and their flags)
@@ -508,7 +545,70 @@ def extra_rows(torch, ff, inputs, e, dev, peaks):
     del A64, X64, Xall
     torch.cuda.empty_cache()
     out.update(batched_rows(torch, ff, inputs, dev, peaks))
+    alu = alu_peaks(torch, ff, dev)
+    out["alu_peaks"] = alu
+    out.update(gemm_rows(torch, ff, inputs, dev, fp32_measured=alu["f32_fma_lane_ops_s"]))
     return out
+
+
+def alu_peaks(torch, ff, dev):
+    """FP32 and FP64 FMA throughput measured by the library's probe kernel
+    (eight independent chains per thread, 8 x 256-thread blocks per SM)."""
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks, threads = 8 * sms, 256
+    out = {}
+    for name, f64, iters in (("f32", False, 1 << 15), ("f64", True, 1 << 10)):
+        buf = torch.empty(blocks * threads, dtype=torch.float64 if f64 else torch.float32, device=dev)
+        t = time_fn(torch, lambda: ff.fma_peak(f64, iters, blocks, threads, out=buf), 5, warm=2)
+        flops = 16 * iters * blocks * threads
+        out[name + "_fma_flop_s"] = flops / t
+        out[name + "_fma_lane_ops_s"] = flops / 2 / t
+    out["sms"] = sms
+    return out
+
+
+def gemm_rows(torch, ff, inputs, dev, size=4096, fp32_measured=None):
+    """Float-float GEMM, size^3: ff_gemm forward and the two adjoint GEMMs of
+    FFGemm, against cuBLAS FP64 and FP32 GEMM (torch.matmul) on the same
+    values.  The kernel is bound by FP32 instruction issue: 28 FP32
+    instructions per term (Mul22 12, Add22 16) against SMs x 128 lanes x the
+    SM clock sampled while it runs."""
+    m = n = k = size
+    g = inputs.gemm(m, n, k, inputs.seed_for(6, 0), device=dev)
+    C = torch.empty((m, n, 2), dtype=torch.float32, device=dev)
+    clk = ClockSampler(dev.index or 0)
+    clk.start()
+    t_fwd = time_fn(torch, lambda: ff.gemm(g.A, g.B, out=C), 5, warm=2)
+    clocks = clk.stop()
+    dA = torch.empty_like(g.A)
+    dB = torch.empty_like(g.B)
+    t_dA = time_fn(torch, lambda: ff.gemm(g.dC, g.B, transb=True, out=dA), 3, warm=1)
+    t_dB = time_fn(torch, lambda: ff.gemm(g.A, g.dC, transa=True, out=dB), 3, warm=1)
+    terms = m * n * k
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = clocks.get("sm_mhz") or 2070.0
+    issue = sms * 128 * mhz * 1e6
+    A64 = inputs.ff_to_f64(g.A)
+    B64 = inputs.ff_to_f64(g.B)
+    del g, dA, dB
+    torch.cuda.empty_cache()
+    t64 = time_fn(torch, lambda: torch.matmul(A64, B64), 3, warm=1)
+    A32, B32 = A64.float(), B64.float()
+    del A64, B64
+    tf32_prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    t32 = time_fn(torch, lambda: torch.matmul(A32, B32), 5, warm=2)
+    torch.backends.cuda.matmul.allow_tf32 = tf32_prev
+    del A32, B32, C
+    torch.cuda.empty_cache()
+    return {f"gemm_{size}^3": {
+        "fwd_ms": round(t_fwd * 1e3, 3), "dA_ms": round(t_dA * 1e3, 3), "dB_ms": round(t_dB * 1e3, 3),
+        "fwd_ff_op_s": 2 * terms / t_fwd, "terms_per_s": terms / t_fwd,
+        "frac_fp32_issue": round(28 * terms / t_fwd / issue, 4), "issue_peak_lane_ops_s": issue,
+        "frac_of_measured_fp32_fma": round(28 * terms / t_fwd / fp32_measured, 4) if fp32_measured else None,
+        "clocks": clocks,
+        "cublas_f64_ms": round(t64 * 1e3, 3), "speedup_vs_cublas_f64": round(t64 / t_fwd, 3),
+        "cublas_f32_ms": round(t32 * 1e3, 3), "slowdown_vs_cublas_f32": round(t_fwd / t32, 2)}}
 
 
 def batched_rows(torch, ff, inputs, dev, peaks):
@@ -713,11 +813,11 @@ def run_reference(args):
     import oracle
     from paper_cs_0603115_gb300 import inputs
     oracle.build()
-    n = 1 << 22
+    n = 1 << 24
     e = inputs.elementwise(n, inputs.seed_for(1, 0))
     a, b, ab, asq = (t.numpy() for t in (e.a, e.b, e.ab, e.a_sqrt))
-    fns = [lambda: oracle.add12(ab), lambda: oracle.mul12(ab), lambda: oracle.add22(a, b),
-           lambda: oracle.mul22(a, b), lambda: oracle.div22(a, b), lambda: oracle.sqrt22(asq)]
+    cores = host_cores()
+    fns, pool = oracle_ops(a, b, ab, asq, cores)
     for _ in range(args.warmup):
         for f in fns:
             f()
@@ -726,16 +826,19 @@ def run_reference(args):
         for f in fns:
             f()
     dt = time.perf_counter() - t0
+    if pool is not None:
+        pool.shutdown()
     value = len(fns) * n * args.steps / dt
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n_values": N_ELEM, "ops_per_step": OPS,
-                   "sample_per_step": "2^22 values of the same generator (the full 2^28 per step would take "
-                                      "minutes on one core)"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"2^22 values per operator per step, {args.steps} steps"},
+                   "sample_per_step": f"2^24 values of the same generator on {cores} host threads (the full "
+                                      "2^28 per step would take minutes)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"2^24 values per operator per step, {args.steps} steps, {cores} threads, "
+                                   "contiguous chunks"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -776,6 +879,11 @@ def run_case(args):
             oy += mm
         plan = batch.BatchPlan(batch.make_instances(specs), tune=(256, 128, 4, 2))
         fn = plan.run
+    elif args.case == "gemm":
+        # --n is the matrix order here: C (n x n) = A (n x n) B (n x n)
+        g = inputs.gemm(n, n, n, inputs.seed_for(6, 0), device=dev)
+        C = torch.empty_like(g.A)
+        fn = lambda: ff.gemm(g.A, g.B, out=C)
     elif args.case in ("gemv", "gemv_t"):
         m = int(math.isqrt(n))
         gi = inputs.gemv(m, m, args.k, inputs.seed_for(4, 0), device=dev)

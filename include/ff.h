@@ -225,6 +225,28 @@ FF_API ff_status ff_gemv_t(const ff2* A, int64_t m, int64_t n, int64_t lda, cons
 FF_API ff_status ff_gemv_dA(const ff2* dY, int64_t m, int64_t lddy, const ff2* X, int64_t n, int64_t ldx,
                             int64_t k, ff2* dA, int64_t ldda, cudaStream_t s);
 
+/* Float-float matrix product (a GEMV with many right-hand sides; not in the
+ * paper): C = op(A) op(B) with
+ *   C[i, j] = acc over p = 0 .. k-1 of Add22(acc, Mul22(op(A)[i, p], op(B)[p, j])),
+ * acc starting at (0, 0), p in increasing order (Section 4.1 operators).
+ * The order does not depend on the launch, so every element is bit-identical
+ * to that plain loop; its error is at most k 2^-44 sum_p |op(A)[i,p] op(B)[p,j]|.
+ * All matrices are row-major device arrays owned by the caller:
+ *   op(A) is m x k: A[i * lda + p] (transa = 0, lda >= k) or A[p * lda + i]
+ *     (transa = 1: A is stored k x m, lda >= m);
+ *   op(B) is k x n: B[p * ldb + j] (transb = 0, ldb >= n) or B[j * ldb + p]
+ *     (transb = 1: B is stored n x k, ldb >= k);
+ *   C is m x n, C[i * ldc + j] (ldc >= n), overwritten; it must not overlap A
+ *     or B.
+ * k = 0 writes (0, 0) to C; m = 0 or n = 0 is a no-op (no pointer is
+ * checked or read).  Negative sizes,
+ * transa / transb other than 0 or 1, short leading dimensions or NULL /
+ * non-8-byte-aligned pointers return FF_ERR_INVALID_ARG before anything is
+ * enqueued.  The adjoints of C = A B are dA = dC B^T (transb = 1) and
+ * dB = A^T dC (transa = 1). */
+FF_API ff_status ff_gemm(int transa, int transb, int64_t m, int64_t n, int64_t k, const ff2* A, int64_t lda,
+                         const ff2* B, int64_t ldb, ff2* C, int64_t ldc, cudaStream_t s);
+
 /* ------------------------------------------------------------------------ */
 /* Batched dot / AXPY: many instances in one persistent launch               */
 /* ------------------------------------------------------------------------ */
@@ -348,6 +370,23 @@ FF_API ff_status ff_f32_add(const float* a, const float* b, float* out, size_t n
 FF_API ff_status ff_f32_mul(const float* a, const float* b, float* out, size_t n, cudaStream_t s);
 FF_API ff_status ff_f32_mad(const float* a, const float* b, const float* c, float* out, size_t n,
                      cudaStream_t s);
+
+/* ------------------------------------------------------------------------ */
+/* Measurement                                                               */
+/* ------------------------------------------------------------------------ */
+
+/* FMA throughput probe (not in the paper: it measures the arithmetic peak
+ * that the FP32-issue-bound kernels and the FP64 baselines are compared
+ * with).  Launches `blocks` x `threads` threads; each runs eight independent
+ * chains x <- fma(x, 1, 1) (binary32 when f64 == 0, binary64 when f64 == 1)
+ * for `iters` rounds and writes the sum of its chains, x_0 + ... + x_7 +
+ * 8 iters with x_c starting at c, to out[thread] (a device array of
+ * blocks * threads floats or doubles, 8-byte aligned, owned by the caller).
+ * One launch performs 16 * iters * blocks * threads floating-point
+ * operations; the caller times it (CUDA events on `s`).  Invalid arguments
+ * (f64 not 0/1, iters < 0, blocks < 1, threads not a multiple of 32 in
+ * 32..1024, NULL or misaligned out) return FF_ERR_INVALID_ARG. */
+FF_API ff_status ff_fma_peak(int f64, int64_t iters, int blocks, int threads, void* out, cudaStream_t s);
 
 /* ------------------------------------------------------------------------ */
 /* Status                                                                    */

@@ -25,9 +25,10 @@ from ._lib import FFError, ff2
 
 __all__ = [
     "add12", "mul12", "add", "add_accurate", "sum2", "dot2", "mul", "div", "sqrt", "axpy", "sum", "dot", "dot_backward",
-    "gemv", "gemv_t", "gemv_dA", "FFDot", "FFGemv", "ffdot", "ffgemv", "FFError", "workspace",
+    "gemv", "gemv_t", "gemv_dA", "gemm", "FFDot", "FFGemv", "FFGemm", "ffdot", "ffgemv", "ffgemm", "FFError",
+    "workspace",
     "f64_add", "f64_mul", "f64_div", "f64_sqrt", "f64_dot", "f64_gemv", "f32_add", "f32_mul",
-    "f32_mad", "load",
+    "f32_mad", "fma_peak", "load",
 ]
 
 
@@ -278,6 +279,25 @@ def gemv_dA(dY, X, out=None):
     return out
 
 
+def gemm(A, B, transa=False, transb=False, out=None):
+    """C = op(A) op(B), row-major float-float matrices.  A: (m, k, 2), or
+    (k, m, 2) when transa; B: (k, n, 2), or (n, k, 2) when transb.  Returns C
+    as (m, n, 2)."""
+    _check_ff(A, "ff_gemm")
+    _check_ff(B, "ff_gemm")
+    if A.dim() != 3 or B.dim() != 3:
+        raise ValueError("ff_gemm: expected A and B of shape (rows, cols, 2)")
+    k, m = (A.shape[0], A.shape[1]) if transa else (A.shape[1], A.shape[0])
+    kb, n = (B.shape[1], B.shape[0]) if transb else (B.shape[0], B.shape[1])
+    if kb != k:
+        raise ValueError(f"ff_gemm: inner dimensions differ ({k} and {kb})")
+    if out is None:
+        out = torch.empty((m, n, 2), dtype=torch.float32, device=A.device)
+    _lib.call("ff_gemm", int(bool(transa)), int(bool(transb)), m, n, k, _ptr(A), max(A.shape[1], 1), _ptr(B),
+              max(B.shape[1], 1), _ptr(out), max(n, 1), _stream())
+    return out
+
+
 # ---------------------------------------------------------------------------
 # autograd: hand-written adjoints
 # ---------------------------------------------------------------------------
@@ -318,12 +338,34 @@ class FFGemv(torch.autograd.Function):
         return dA, dX
 
 
+class FFGemm(torch.autograd.Function):
+    """C = A B with the adjoints dA = dC B^T and dB = A^T dC, both ff_gemm
+    launches on the stored operands (no transposed copies)."""
+
+    @staticmethod
+    def forward(ctx, A, B):
+        ctx.save_for_backward(A, B)
+        return gemm(A, B)
+
+    @staticmethod
+    def backward(ctx, dC):
+        A, B = ctx.saved_tensors
+        dC = dC.contiguous()
+        dA = gemm(dC, B, transb=True) if ctx.needs_input_grad[0] else None
+        dB = gemm(A, dC, transa=True) if ctx.needs_input_grad[1] else None
+        return dA, dB
+
+
 def ffdot(x, y):
     return FFDot.apply(x, y)
 
 
 def ffgemv(A, X):
     return FFGemv.apply(A, X)
+
+
+def ffgemm(A, B):
+    return FFGemm.apply(A, B)
 
 
 # ---------------------------------------------------------------------------
@@ -398,4 +440,14 @@ def f32_mad(a, b, c, out=None):
         _f32_check(t, "ff_f32_mad")
     out = torch.empty_like(a) if out is None else out
     _lib.call("ff_f32_mad", _ptr(a), _ptr(b), _ptr(c), _ptr(out), a.numel(), _stream())
+    return out
+
+
+def fma_peak(f64: bool, iters: int, blocks: int, threads: int = 256, device=None, out=None):
+    """Launch the FMA throughput probe (16 * iters * blocks * threads flops);
+    returns the per-thread sums (each 28 + 8 * iters)."""
+    dtype = torch.float64 if f64 else torch.float32
+    if out is None:
+        out = torch.empty(blocks * threads, dtype=dtype, device=device or "cuda")
+    _lib.call("ff_fma_peak", int(bool(f64)), iters, blocks, threads, _ptr(out), _stream())
     return out

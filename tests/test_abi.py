@@ -54,6 +54,18 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert lib.ff_gemv(good, -1, 4, 4, good, 4, 1, good, 4, None) == INVALID
     assert lib.ff_gemv_t(good, 4, 4, 4, good, 3, 1, good, 4, good, 1 << 20, None) == INVALID
     assert lib.ff_f64_add(good, mis, good, 3, None) == INVALID
+    assert lib.ff_gemm(2, 0, 4, 4, 4, good, 4, good, 4, good, 4, None) == INVALID   # transa not 0/1
+    assert lib.ff_gemm(0, 0, 4, 4, 5, good, 4, good, 4, good, 4, None) == INVALID   # lda < k
+    assert lib.ff_gemm(1, 0, 6, 4, 5, good, 5, good, 4, good, 4, None) == INVALID   # transposed: lda < m
+    assert lib.ff_gemm(0, 1, 4, 6, 5, good, 5, good, 4, good, 6, None) == INVALID   # transposed: ldb < k
+    assert lib.ff_gemm(0, 0, 4, 6, 5, good, 5, good, 6, good, 5, None) == INVALID   # ldc < n
+    assert lib.ff_gemm(0, 0, -1, 4, 4, good, 4, good, 4, good, 4, None) == INVALID
+    assert lib.ff_gemm(0, 0, 4, 4, 4, mis, 4, good, 4, good, 4, None) == INVALID
+    assert lib.ff_fma_peak(2, 10, 1, 64, good, None) == INVALID
+    assert lib.ff_fma_peak(0, 10, 1, 48, good, None) == INVALID     # threads not a multiple of 32
+    assert lib.ff_fma_peak(0, -1, 1, 64, good, None) == INVALID
+    assert lib.ff_fma_peak(1, 10, 0, 64, good, None) == INVALID
+    assert lib.ff_fma_peak(1, 10, 1, 64, None, None) == INVALID
 
 
 def test_zero_length_is_a_host_noop(lib):
@@ -61,6 +73,8 @@ def test_zero_length_is_a_host_noop(lib):
     assert lib.ff_add(None, None, None, 0, None) == 0
     assert lib.ff_add12(None, None, 0, None) == 0
     assert lib.ff_f32_add(None, None, None, 0, None) == 0
+    assert lib.ff_gemm(0, 0, 0, 5, 3, None, 3, None, 5, None, 5, None) == 0
+    assert lib.ff_gemm(0, 0, 5, 0, 3, None, 3, None, 1, None, 1, None) == 0
 
 
 def test_product_never_imports_the_oracle():
