@@ -71,6 +71,20 @@ def test_dot2_sum2_replay_bitexact(n, offset):
     same_bits(ff.sum2(x).cpu().numpy(), replay.reduce_replay(terms, gr, h, v, pol))
 
 
+def test_dot2_sum2_full_size_replay_bitexact():
+    """The benchmark's size: 2^26 binary32 values at cond 1e12."""
+    import paper_cs_0603115_gb300 as ff
+    import replay
+    n = 1 << 26
+    g = inputs.ill_dot_f32(n, 1e12, inputs.seed_for(5, 12), device=DEV)
+    xn, yn = g.x.cpu().numpy(), g.y.cpu().numpy()
+    pol = replay.Dot2Policy()
+    gr, h, v = _shape(g.x, g.y)
+    same_bits(ff.dot2(g.x, g.y).cpu().numpy(), replay.reduce_replay(oracle.mul12(np.stack([xn, yn], 1)), gr, h, v, pol))
+    gr, h, v = _shape(g.x, None)
+    same_bits(ff.sum2(g.x).cpu().numpy(), replay.reduce_replay(np.stack([xn, np.zeros_like(xn)], 1), gr, h, v, pol))
+
+
 @pytest.mark.parametrize("cond", [1e3, 1e6, 1e9, 1e12])
 def test_dot2_ill_conditioned_within_bound(cond):
     import paper_cs_0603115_gb300 as ff

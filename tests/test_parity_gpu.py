@@ -165,6 +165,22 @@ def test_dot_and_sum_replay_bitexact(cfg0, n, offset):
     same_bits(ff.sum(x).cpu().numpy(), replay.reduce_replay(xn, g, h, v))
 
 
+def test_dot_and_sum_full_size_replay_bitexact():
+    """At the benchmark's size (2^26 values, cond 1e12), ff_dot and ff_sum
+    match the replay of their documented order bit for bit."""
+    import replay
+    n = 1 << 26
+    g_ = inputs.ill_dot(n, 1e12, inputs.seed_for(2, 12), device=DEV)
+    xn, yn = g_.x.cpu().numpy(), g_.y.cpu().numpy()
+    terms = _oracle_threaded(oracle.mul22, xn, yn)
+    g, h, v = shape_of(g_.x, g_.y)
+    same_bits(ff.dot(g_.x, g_.y).cpu().numpy(), replay.reduce_replay(terms, g, h, v))
+    g, h, v = shape_of(g_.x, None)
+    same_bits(ff.sum(g_.x).cpu().numpy(), replay.reduce_replay(xn, g, h, v))
+    del g_, terms
+    torch.cuda.empty_cache()
+
+
 def test_dot_mixed_alignment_replay(cfg0):
     n = 70001
     x = gpu(cfg0.a[: n + 1])[:n]
@@ -293,6 +309,42 @@ def test_full_size_sampled_bitexact():
     same_bits(take(ff.sqrt(e.a_sqrt, out=out)), oracle.sqrt22(asq))
     # divisor floor of the operators holds for the generated divisors
     assert e.b[:, 0].abs().min().item() >= 2.0 ** -60
+    del out, e
+    torch.cuda.empty_cache()
+
+
+def _oracle_threaded(fn, *arrays, threads=None):
+    """The oracle function over contiguous chunks on all host cores (its C
+    loops release the GIL); the result equals one call on the whole arrays."""
+    import concurrent.futures as cf
+    import os
+    threads = threads or max(1, len(os.sched_getaffinity(0)))
+    n = arrays[0].shape[0]
+    cuts = [n * i // threads for i in range(threads + 1)]
+    with cf.ThreadPoolExecutor(threads) as ex:
+        parts = list(ex.map(lambda i: fn(*(a[cuts[i]:cuts[i + 1]] for a in arrays)), range(threads)))
+    return np.concatenate(parts)
+
+
+def test_full_size_every_value_bitexact():
+    """All 2^28 results of each of the six operators at the benchmark's size,
+    bit for bit against the oracle (in chunks of 2^26 values)."""
+    n = 1 << 28
+    e = inputs.elementwise(n, inputs.seed_for(1, 0), device=DEV)
+    out = torch.empty_like(e.a)
+    cases = [("add12", lambda: ff.add12(e.ab, out=out), oracle.add12, ("ab",)),
+             ("mul12", lambda: ff.mul12(e.ab, out=out), oracle.mul12, ("ab",)),
+             ("add", lambda: ff.add(e.a, e.b, out=out), oracle.add22, ("a", "b")),
+             ("mul", lambda: ff.mul(e.a, e.b, out=out), oracle.mul22, ("a", "b")),
+             ("div", lambda: ff.div(e.a, e.b, out=out), oracle.div22, ("a", "b")),
+             ("sqrt", lambda: ff.sqrt(e.a_sqrt, out=out), oracle.sqrt22, ("a_sqrt",))]
+    chunk = 1 << 26
+    for name, gpu_op, orc_op, keys in cases:
+        gpu_op()
+        torch.cuda.synchronize()
+        for lo in range(0, n, chunk):
+            ins = [getattr(e, k)[lo:lo + chunk].cpu().numpy() for k in keys]
+            same_bits(out[lo:lo + chunk].cpu().numpy(), _oracle_threaded(orc_op, *ins))
     del out, e
     torch.cuda.empty_cache()
 
