@@ -315,8 +315,10 @@ FF_API size_t ff_batch_workspace_bytes(const ff_batch_plan* plan);
 /* The plan's tune, tile count and grid (any pointer may be NULL). */
 FF_API ff_status ff_batch_plan_info(const ff_batch_plan* plan, ff_tune* tune, int64_t* ntiles, unsigned* grid);
 
-/* Run every instance of the plan: one memset of the per-instance counters and
- * one persistent kernel launch on stream s.  Graph-capturable. */
+/* Run every instance of the plan: one memset of the per-instance counters
+ * and the tile counter, and one persistent kernel launch on stream s.
+ * Graph-capturable.  The workspace (ff_batch_workspace_bytes, 16-byte
+ * aligned, owned by the caller) must not be shared by runs that overlap. */
 FF_API ff_status ff_batch_run(const ff_batch_plan* plan, void* ws, size_t ws_bytes, cudaStream_t s);
 
 /* Free the plan's device and host memory (NULL is a no-op).  The caller must

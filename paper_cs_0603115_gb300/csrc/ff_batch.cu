@@ -28,6 +28,13 @@
 //              tile order and writes the result.
 // No block waits for another; the per-instance counters are zeroed by a
 // memset at the start of every run (and left zero by the last tile).
+//
+// Plans made only of GEMV rows run a kernel of their own: their tiles differ
+// in cost (a tile holds 4 x warps x R rows, and R cannot drop below one for
+// rows longer than 16K / (4 x warps) values), so the plan sorts the tiles by
+// cost, largest first, and the blocks take the next tile from an atomic
+// counter (zeroed by the same memset) instead of round robin.  Each such
+// tile writes whole rows, so the order changes no result.
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -181,7 +188,7 @@ __device__ __noinline__ void gemv_rows_tile(const float2* A, const float2* xv, f
 template <int BLOCK, int PPT, int UN, bool GEMV_ROWS>
 __global__ void __launch_bounds__(BLOCK)
 batch_kernel(const DevInst* __restrict__ insts, const Tile* __restrict__ tiles, int64_t ntiles,
-             float2* __restrict__ partials, unsigned* __restrict__ counters)
+             float2* __restrict__ partials, unsigned* __restrict__ counters, unsigned long long*)
 {
     __shared__ float2 sm[BLOCK / 32];
     __shared__ int is_last;
@@ -358,16 +365,22 @@ batch_kernel(const DevInst* __restrict__ insts, const Tile* __restrict__ tiles, 
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK)
 batch_gemv_kernel(const DevInst* __restrict__ insts, const Tile* __restrict__ tiles, int64_t ntiles,
-                  float2* __restrict__, unsigned* __restrict__)
+                  float2* __restrict__, unsigned* __restrict__, unsigned long long* __restrict__ next)
 {
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    __shared__ unsigned long long s_t;
+    for (;;) {
+        if (threadIdx.x == 0) s_t = atomicAdd(next, 1ull);
+        __syncthreads();
+        const unsigned long long t = s_t;
+        __syncthreads();  // every thread has read s_t before thread 0 takes the next tile
+        if (t >= static_cast<unsigned long long>(ntiles)) break;
         const Tile tl = tiles[t];
         const DevInst& I = insts[tl.inst];
         gemv_rows_tile_body(I.x, I.y, I.out, I.n, I.lda, I.m, I.vec, I.rows_per_warp, tl.start);
     }
 }
 
-using KernelFn = void (*)(const DevInst*, const Tile*, int64_t, float2*, unsigned*);
+using KernelFn = void (*)(const DevInst*, const Tile*, int64_t, float2*, unsigned*, unsigned long long*);
 
 struct Variant {
     int block;
@@ -403,10 +416,14 @@ KernelFn kernel_for(const Variant& v, const ff_batch_plan& p)
     return p.only_gemv_rows ? v.fn_gemv_only : (p.has_gemv_rows ? v.fn_gemv : v.fn);
 }
 
+// Workspace: the per-record counters (4 B each), the tile scheduler's 8-byte
+// counter after them, padded to kCountersAlign; then one partial per tile.
+size_t sched_offset(size_t nrec) { return (nrec * 4 + 7) / 8 * 8; }
+size_t counters_bytes(size_t nrec) { return (sched_offset(nrec) + 8 + kCountersAlign - 1) / kCountersAlign * kCountersAlign; }
+
 size_t ws_bytes_for(const ff_batch_plan* p)
 {
-    const size_t counters = ((static_cast<size_t>(p->count) * 4 + kCountersAlign - 1) / kCountersAlign) * kCountersAlign;
-    return counters + static_cast<size_t>(p->ntiles) * sizeof(float2) + 16;
+    return counters_bytes(static_cast<size_t>(p->count)) + static_cast<size_t>(p->ntiles) * sizeof(float2) + 16;
 }
 
 ff_status validate(const ff_batch_instance* inst, int count)
@@ -537,6 +554,17 @@ ff_status ff_batch_plan_create(const ff_batch_instance* inst, int count, const f
         p->has_gemv_rows |= (r.kind == kGemvRows);
         p->only_gemv_rows &= (r.kind == kGemvRows);
     }
+    if (p->only_gemv_rows) {
+        // largest tiles first (values + a fixed cost per row of 64 values),
+        // taken in this order by the blocks of the GEMV-only kernel
+        const int64_t warps = tune.block / 32;
+        auto cost = [&](const Tile& t) {
+            const DevInst& d = hi[static_cast<size_t>(t.inst)];
+            const int64_t rows = std::min<int64_t>(4 * warps * d.rows_per_warp, d.m - t.start);
+            return rows * (d.n + 64);
+        };
+        std::stable_sort(ht.begin(), ht.end(), [&](const Tile& a, const Tile& b) { return cost(a) > cost(b); });
+    }
     p->tune = tune;
     p->ntiles = static_cast<int64_t>(ht.size());
     p->ndot = ndot;
@@ -588,11 +616,13 @@ ff_status ff_batch_run(const ff_batch_plan* p, void* ws, size_t ws_bytes, cudaSt
     const Variant* var = find_variant(p->tune);
     if (!var) return FF_ERR_INVALID_ARG;
     auto* counters = static_cast<unsigned*>(ws);
-    const size_t cbytes = ((static_cast<size_t>(p->count) * 4 + kCountersAlign - 1) / kCountersAlign) * kCountersAlign;
-    auto* partials = reinterpret_cast<float2*>(static_cast<char*>(ws) + cbytes);
-    ff_status st = ffh::cuda_status(cudaMemsetAsync(counters, 0, static_cast<size_t>(p->count) * 4, s));
+    const size_t so = sched_offset(static_cast<size_t>(p->count));
+    auto* next = reinterpret_cast<unsigned long long*>(static_cast<char*>(ws) + so);
+    auto* partials = reinterpret_cast<float2*>(static_cast<char*>(ws) + counters_bytes(static_cast<size_t>(p->count)));
+    ff_status st = ffh::cuda_status(cudaMemsetAsync(counters, 0, so + 8, s));
     if (st != FF_OK) return st;
-    kernel_for(*var, *p)<<<p->grid, p->tune.block, 0, s>>>(p->d_inst, p->d_tiles, p->ntiles, partials, counters);
+    kernel_for(*var, *p)<<<p->grid, p->tune.block, 0, s>>>(p->d_inst, p->d_tiles, p->ntiles, partials, counters,
+                                                           next);
     return ffh::check_launch();
 }
 
@@ -681,8 +711,7 @@ size_t ff_batch_autotune_workspace_bytes(const ff_batch_instance* inst, int coun
         ntiles += reps * static_cast<size_t>(n > 0 ? (n + smallest - 1) / smallest : 1);
         nrec += reps;
     }
-    const size_t counters = ((nrec * 4 + kCountersAlign - 1) / kCountersAlign) * kCountersAlign;
-    return counters + ntiles * sizeof(float2) + 16;
+    return counters_bytes(nrec) + ntiles * sizeof(float2) + 16;
 }
 
 ff_status ff_batch_autotune(const ff_batch_instance* inst, int count, void* ws, size_t ws_bytes, cudaStream_t s,

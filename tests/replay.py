@@ -127,3 +127,42 @@ def reduce_replay(terms: np.ndarray, grid: int, head: int, vector: bool, pol=Non
         sl = part[b0:b0 + BLOCK]
         acc2[: sl.shape[0]] = pol.combine(acc2[: sl.shape[0]], sl)
     return pol.finalize(_block_tree(pol, acc2.reshape(1, BLOCK, 2))[0])
+
+
+def gemv_rows8_replay(A, x, vec: bool):
+    """Rows of a batched GEMV reduced by eight lanes each (ff_batch.cu, the
+    GEMV-rows tile): lane l of the row takes the two-value chunks l + 16i into
+    its first and l + 8 + 16i into its second accumulator while both fit, a
+    leftover chunk l + 16i into the first; adds the two; with an odd length,
+    lane 0 adds the last term; then the shuffle-down Add22 tree over offsets
+    4, 2, 1.  Without 16-byte access (vec False) lane l takes the terms
+    l + 8i into one accumulator.  A: (m, n, 2), x: (n, 2); returns (m, 2)."""
+    A = np.ascontiguousarray(A, np.float32)
+    x = np.ascontiguousarray(x, np.float32)
+    m, n = A.shape[0], A.shape[1]
+    terms = oracle.mul22(A.reshape(-1, 2), np.tile(x, (m, 1))).reshape(m, n, 2) if m * n else np.zeros((m, n, 2), f32)
+    add = lambda a, b: oracle.add22(np.ascontiguousarray(a), np.ascontiguousarray(b))
+    acc = np.zeros((m, 8, 2), f32)
+    if vec:
+        acc1 = np.zeros((m, 8, 2), f32)
+        nch = n // 2
+        for l in range(8):
+            c = l
+            while c + 8 < nch:
+                acc[:, l] = add(add(acc[:, l], terms[:, 2 * c]), terms[:, 2 * c + 1])
+                acc1[:, l] = add(add(acc1[:, l], terms[:, 2 * (c + 8)]), terms[:, 2 * (c + 8) + 1])
+                c += 16
+            while c < nch:
+                acc[:, l] = add(add(acc[:, l], terms[:, 2 * c]), terms[:, 2 * c + 1])
+                c += 8
+            acc[:, l] = add(acc[:, l], acc1[:, l])
+        if n & 1:
+            acc[:, 0] = add(acc[:, 0], terms[:, n - 1])
+    else:
+        for l in range(8):
+            for j in range(l, n, 8):
+                acc[:, l] = add(acc[:, l], terms[:, j])
+    for off in (4, 2, 1):
+        for l in range(off):
+            acc[:, l] = add(acc[:, l], acc[:, l + off])
+    return acc[:, 0]

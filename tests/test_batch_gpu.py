@@ -198,3 +198,37 @@ def test_batch_gemv_instances(tune):
             else:
                 assert got[r, 0] == 0 and got[r, 1] == 0
     plan.close()
+
+
+@pytest.mark.parametrize("tune", [None, (128, 16, 0), (512, 64, 2), (256, 32, 0, 2)])
+def test_batch_gemv_only_plan_bitexact(tune):
+    """A plan made only of GEMV rows (its own kernel: tiles sorted by cost,
+    taken from an atomic counter): every row bit for bit equal to the replay
+    of the eight-lane row order, on a plain run and on two graph replays."""
+    from paper_cs_0603115_gb300 import batch
+    import replay
+    shapes = [(1, 1), (3, 1000), (17, 4097), (64, 9), (0, 5), (5, 0), (33, 64), (7, 4096), (129, 32),
+              (2, 65536), (300, 3)]
+    specs, keep = [], []
+    for i, (m, n) in enumerate(shapes):
+        gi = inputs.gemv(m, n, 1, inputs.seed_for(4, 110 + i))
+        A, x = gi.A.to(DEV), gi.X[0].to(DEV).contiguous()
+        out = torch.full((m, 2), float("nan"), dtype=torch.float32, device=DEV)
+        specs.append((batch.GEMV, A, x, out, None))
+        keep.append((gi.A.numpy(), gi.X[0].numpy(), out, n % 2 == 0))
+    plan = batch.BatchPlan(batch.make_instances(specs), tune=tune)
+    plan.run()
+    torch.cuda.synchronize()
+    want = [replay.gemv_rows8_replay(An, xn, vec) for An, xn, _, vec in keep]
+    for (An, xn, out, vec), w in zip(keep, want):
+        same_bits(out.cpu().numpy(), w)
+        out.fill_(float("nan"))
+    plan.capture()
+    for _ in range(2):
+        plan.launch()
+        torch.cuda.synchronize()
+        for (An, xn, out, vec), w in zip(keep, want):
+            same_bits(out.cpu().numpy(), w)
+            out.fill_(float("nan"))
+    plan.close()
+
