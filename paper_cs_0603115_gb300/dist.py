@@ -80,3 +80,20 @@ def sharded_gemv_t(A_local: torch.Tensor, dY_local: torch.Tensor, group=None, ge
     for r in range(1, parts.shape[0]):
         acc = add_fn(acc, parts[r].contiguous())
     return acc
+
+
+def partition_instances(nbytes, world: int) -> list[list[int]]:
+    """Byte-balanced split of batched instances over `world` ranks: instances
+    in decreasing order of bytes, each to the rank with the fewest bytes so
+    far (ties: the lowest rank); every rank's list is returned in increasing
+    instance order.  The busiest rank carries at most the average plus the
+    largest instance."""
+    import heapq
+    order = sorted(range(len(nbytes)), key=lambda i: (-int(nbytes[i]), i))
+    heap = [(0, r) for r in range(world)]
+    parts = [[] for _ in range(world)]
+    for i in order:
+        load, r = heapq.heappop(heap)
+        parts[r].append(i)
+        heapq.heappush(heap, (load + int(nbytes[i]), r))
+    return [sorted(p) for p in parts]

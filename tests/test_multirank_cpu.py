@@ -118,3 +118,19 @@ def test_shard_ranges_cover_exactly():
             assert spans[0][0] == 0 and spans[-1][1] == n
             assert all(a[1] == b[0] for a, b in zip(spans, spans[1:]))
             assert max(h - l for l, h in spans) - min(h - l for l, h in spans) <= 1
+
+
+def test_partition_instances_balances_bytes():
+    from paper_cs_0603115_gb300 import dist as ffdist
+    from paper_cs_0603115_gb300 import inputs
+    lengths, kinds = inputs.batch_lengths(4096, inputs.seed_for(3, 0))
+    nbytes = [16 * n if k == 0 else 24 * n for n, k in zip(lengths, kinds)]
+    for world in (1, 2, 3, 8):
+        parts = ffdist.partition_instances(nbytes, world)
+        assert sorted(i for p in parts for i in p) == list(range(len(nbytes)))
+        loads = [sum(nbytes[i] for i in p) for p in parts]
+        assert max(loads) <= sum(nbytes) / world + max(nbytes)
+        assert all(p == sorted(p) for p in parts)
+    assert ffdist.partition_instances([], 4) == [[], [], [], []]
+    assert ffdist.partition_instances([5, 5, 5, 5], 2) == [[0, 2], [1, 3]]
+
