@@ -59,18 +59,20 @@ def _nvals(t: torch.Tensor) -> int:
 
 
 # ---------------------------------------------------------------------------
-# workspace (caller-owned device scratch, cached per device)
+# workspace (caller-owned device scratch, cached per device and stream)
 # ---------------------------------------------------------------------------
 _ws_cache: dict = {}
 
 
 def workspace(nbytes: int, device=None, key: str = "reduce") -> torch.Tensor:
-    """A cached uint8 device buffer of at least ``nbytes`` (16-byte aligned).
+    """A cached uint8 device buffer of at least ``nbytes`` (16-byte aligned)
+    for calls on the current stream.
 
-    Buffers are shared by calls on the same device and key: do not run two
-    reductions that share one concurrently on different streams."""
+    Each (device, stream, key) has its own buffer, allocated while that
+    stream is current, so calls on one stream reuse it in stream order and
+    calls on different streams never share one."""
     dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
-    k = (dev.index, key)
+    k = (dev.index, torch.cuda.current_stream(dev).cuda_stream, key)
     buf = _ws_cache.get(k)
     if buf is None or buf.numel() < nbytes:
         buf = torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=dev)
