@@ -103,8 +103,12 @@ ff_status launch_gemv_tile(const float2* A, int64_t m, int64_t n, int64_t lda, c
     return ffh::check_launch();
 }
 
-// Largest supported tile width <= k.
-inline int tile_for(int64_t k) { return k >= 16 ? 16 : k >= 8 ? 8 : k >= 4 ? 4 : k >= 2 ? 2 : 1; }
+// Tile width for the float-float kernels: up to seven right-hand sides in
+// one pass (one read of A: below eight the kernels are issue-bound only
+// once all k share the pass), else 8 or 16; any k takes at most one
+// remainder pass.  The FP64 baseline uses powers of two.
+inline int tile_for(int64_t k) { return k >= 16 ? 16 : k >= 8 ? 8 : static_cast<int>(k); }
+inline int f64_tile_for(int64_t k) { return k >= 16 ? 16 : k >= 8 ? 8 : k >= 4 ? 4 : k >= 2 ? 2 : 1; }
 
 // ---------------------------------------------------------------------------
 // dX = A^T dY
@@ -209,8 +213,16 @@ const void* gemv_t_kernel_ptr(int kt, bool vec)
                         : reinterpret_cast<const void*>(&gemv_t_kernel<16, false>);
     case 8: return vec ? reinterpret_cast<const void*>(&gemv_t_kernel<8, true>)
                        : reinterpret_cast<const void*>(&gemv_t_kernel<8, false>);
+    case 7: return vec ? reinterpret_cast<const void*>(&gemv_t_kernel<7, true>)
+                       : reinterpret_cast<const void*>(&gemv_t_kernel<7, false>);
+    case 6: return vec ? reinterpret_cast<const void*>(&gemv_t_kernel<6, true>)
+                       : reinterpret_cast<const void*>(&gemv_t_kernel<6, false>);
+    case 5: return vec ? reinterpret_cast<const void*>(&gemv_t_kernel<5, true>)
+                       : reinterpret_cast<const void*>(&gemv_t_kernel<5, false>);
     case 4: return vec ? reinterpret_cast<const void*>(&gemv_t_kernel<4, true>)
                        : reinterpret_cast<const void*>(&gemv_t_kernel<4, false>);
+    case 3: return vec ? reinterpret_cast<const void*>(&gemv_t_kernel<3, true>)
+                       : reinterpret_cast<const void*>(&gemv_t_kernel<3, false>);
     case 2: return vec ? reinterpret_cast<const void*>(&gemv_t_kernel<2, true>)
                        : reinterpret_cast<const void*>(&gemv_t_kernel<2, false>);
     default: return vec ? reinterpret_cast<const void*>(&gemv_t_kernel<1, true>)
@@ -348,7 +360,11 @@ ff_status ff_gemv(const ff2* A_, int64_t m, int64_t n, int64_t lda, const ff2* X
         switch (kt) {
         case 16: st = launch_gemv_tile<16>(A, m, n, lda, Xc, ldx, Yc, ldy, vec, s); break;
         case 8: st = launch_gemv_tile<8>(A, m, n, lda, Xc, ldx, Yc, ldy, vec, s); break;
+        case 7: st = launch_gemv_tile<7>(A, m, n, lda, Xc, ldx, Yc, ldy, vec, s); break;
+        case 6: st = launch_gemv_tile<6>(A, m, n, lda, Xc, ldx, Yc, ldy, vec, s); break;
+        case 5: st = launch_gemv_tile<5>(A, m, n, lda, Xc, ldx, Yc, ldy, vec, s); break;
         case 4: st = launch_gemv_tile<4>(A, m, n, lda, Xc, ldx, Yc, ldy, vec, s); break;
+        case 3: st = launch_gemv_tile<3>(A, m, n, lda, Xc, ldx, Yc, ldy, vec, s); break;
         case 2: st = launch_gemv_tile<2>(A, m, n, lda, Xc, ldx, Yc, ldy, vec, s); break;
         default: st = launch_gemv_tile<1>(A, m, n, lda, Xc, ldx, Yc, ldy, vec, s); break;
         }
@@ -403,7 +419,11 @@ ff_status ff_gemv_t(const ff2* A_, int64_t m, int64_t n, int64_t lda, const ff2*
         switch (kt) {
         case 16: launch_gemv_t_tile<16>(A, mm, n, lda, dYc, lddy, rpb, nrb, out, out_ld, rb_stride, vec, s); break;
         case 8: launch_gemv_t_tile<8>(A, mm, n, lda, dYc, lddy, rpb, nrb, out, out_ld, rb_stride, vec, s); break;
+        case 7: launch_gemv_t_tile<7>(A, mm, n, lda, dYc, lddy, rpb, nrb, out, out_ld, rb_stride, vec, s); break;
+        case 6: launch_gemv_t_tile<6>(A, mm, n, lda, dYc, lddy, rpb, nrb, out, out_ld, rb_stride, vec, s); break;
+        case 5: launch_gemv_t_tile<5>(A, mm, n, lda, dYc, lddy, rpb, nrb, out, out_ld, rb_stride, vec, s); break;
         case 4: launch_gemv_t_tile<4>(A, mm, n, lda, dYc, lddy, rpb, nrb, out, out_ld, rb_stride, vec, s); break;
+        case 3: launch_gemv_t_tile<3>(A, mm, n, lda, dYc, lddy, rpb, nrb, out, out_ld, rb_stride, vec, s); break;
         case 2: launch_gemv_t_tile<2>(A, mm, n, lda, dYc, lddy, rpb, nrb, out, out_ld, rb_stride, vec, s); break;
         default: launch_gemv_t_tile<1>(A, mm, n, lda, dYc, lddy, rpb, nrb, out, out_ld, rb_stride, vec, s); break;
         }
@@ -454,7 +474,7 @@ ff_status ff_f64_gemv(const double* A, int64_t m, int64_t n, int64_t lda, const 
     if (m == 0) return FF_OK;
     const unsigned grid = static_cast<unsigned>((m + kGWarps - 1) / kGWarps);
     for (int64_t c0 = 0; c0 < k;) {
-        const int kt = tile_for(k - c0);
+        const int kt = f64_tile_for(k - c0);
         const double* Xc = X + c0 * ldx;
         double* Yc = Y + c0 * ldy;
         switch (kt) {
