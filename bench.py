@@ -470,6 +470,18 @@ def extra_rows(torch, ff, inputs, e, dev, peaks):
                            "frac_hbm": round(24 * n / t / 1e9 / hbm, 4), "ff_op_s": n / t}
     del oacc
     torch.cuda.empty_cache()
+    # the reductions at the elementwise size (2^28 values of the same arrays):
+    # the fixed cost of a launch (ticket memset, ramp, last-block combine) is
+    # a quarter of its share at 2^26
+    a32, b32 = e.a[:, 0].contiguous(), e.b[:, 0].contiguous()
+    for name, fn, nb, ops in (("dot_2^28", lambda: ff.dot(e.a, e.b), 16, 2),
+                              ("sum_2^28", lambda: ff.sum(e.a), 8, 1),
+                              ("dot2_f32_2^28", lambda: ff.dot2(a32, b32), 8, 2)):
+        t = time_fn(torch, fn, 10)
+        out[name] = {"ms": round(t * 1e3, 4), "GB/s": round(nb * n / t / 1e9, 1),
+                     "frac_hbm": round(nb * n / t / 1e9 / hbm, 4), "ops_s": ops * n / t}
+    del a32, b32
+    torch.cuda.empty_cache()
     # compensated Sum2 / Dot2 of binary32 vectors, n = 2^26 (4 / 8 B per value)
     nd2 = 1 << 26
     g2 = inputs.ill_dot_f32(nd2, 1e12, inputs.seed_for(5, 12), device=dev)
@@ -725,11 +737,26 @@ def batched_rows(torch, ff, inputs, dev, peaks):
     tb_plain = time_fn(torch, plain_b, 3, warm=1)
     tf = time_fn(torch, pf.launch, 5)
     tb = time_fn(torch, pb.launch, 5)
+    # accuracy of the batched forms against the plain calls: the forward's
+    # difference over sum |x_i y_i| (both within the dot bound), the adjoint
+    # bit for bit (it is the same Mul22 per value)
+    torch.cuda.synchronize()
+    fwd_rel, grad_equal = 0.0, True
+    for i in dots:
+        xv, yv = inputs.ff_to_f64(X[sl[i]]), inputs.ff_to_f64(Y[sl[i]])
+        a = float((xv * yv).abs().sum().item())
+        d = abs((float(D[i, 0]) - float(Dplain[i, 0])) + (float(D[i, 1]) - float(Dplain[i, 1])))
+        fwd_rel = max(fwd_rel, d / a if a > 0 else d)
+        dx, dy = ff.dot_backward(dout[i], X[sl[i]], Y[sl[i]])
+        grad_equal &= bool(torch.equal(dx.view(torch.int32), Z[sl[i]].view(torch.int32)) and
+                           torch.equal(dy.view(torch.int32), W[sl[i]].view(torch.int32)))
+        del xv, yv, dx, dy
     rows["batched_2048_dot_fwd_grad"] = {
         "values": nd, "fwd_plain_ms": round(tf_plain * 1e3, 3), "fwd_batched_graph_ms": round(tf * 1e3, 3),
         "bwd_plain_ms": round(tb_plain * 1e3, 3), "bwd_batched_graph_ms": round(tb * 1e3, 3),
         "fwd_speedup": round(tf_plain / tf, 3), "bwd_speedup": round(tb_plain / tb, 3),
-        "fwd_frac_hbm": round(16 * nd / tf / 1e9 / hbm, 4), "bwd_frac_hbm": round(32 * nd / tb / 1e9 / hbm, 4)}
+        "fwd_frac_hbm": round(16 * nd / tf / 1e9 / hbm, 4), "bwd_frac_hbm": round(32 * nd / tb / 1e9 / hbm, 4),
+        "fwd_max_absdiff_vs_plain_over_sum_abs": fwd_rel, "grad_bitequal_plain": grad_equal}
     pf.close()
     pb.close()
     del X, Y, Z, W, D, Dplain, dout
