@@ -341,6 +341,21 @@ def test_div22_accuracy(orc):
     assert orc.relerr("div", a, b, r).max() <= 2.0 ** -43
 
 
+def test_div22_sqrt22_bruteforce(orc):
+    """Every ordered pair of the float-float subset (extreme significands,
+    exponents -30..30, low parts 0, about ulp/2 and 2^-30 hi): Div22 within
+    2^-44 of the exact quotient, and Sqrt22 of every subset value (made
+    non-negative) within 2^-44 of the exact square root (binary128)."""
+    F = ff_subset()
+    i, j = np.meshgrid(np.arange(F.shape[0]), np.arange(F.shape[0]), indexing="ij")
+    a, b = F[i.ravel()], F[j.ravel()]
+    r = orc.div22(a, b)
+    assert orc.relerr("div", a, b, r).max() <= 2.0 ** -44
+    s = F.copy()
+    s[s[:, 0] < 0] *= -1
+    assert orc.relerr("sqrt", s, None, orc.sqrt22(s)).max() <= 2.0 ** -44
+
+
 def test_sqrt22_special_cases(orc):
     r = orc.sqrt22(ff((4.0, 0.0), (0.0, 0.0), (-0.0, 0.0), (-1.0, 0.0),
                       (1 + 2.0 ** -19, 2.0 ** -40), (9.0, 0.0), (2.0 ** -40, 0.0)))

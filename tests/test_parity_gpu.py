@@ -313,6 +313,30 @@ def test_full_size_sampled_bitexact():
     torch.cuda.empty_cache()
 
 
+def test_bruteforce_subsets_bitexact():
+    """Every ordered pair of the oracle pins' brute-force subsets (extreme
+    significands 0x800000..0x80000F and 0xFFFFF0..0xFFFFFF, exponents -30..30,
+    both signs; float-float values with low parts 0, about ulp/2 and 2^-30
+    hi), bit for bit on the GPU."""
+    import test_oracle_pins as pins
+    S = pins.subset_floats()
+    ab = pins.all_pairs(S)
+    abd = gpu(torch.from_numpy(ab))
+    same_bits(ff.add12(abd).cpu().numpy(), oracle.add12(ab))
+    same_bits(ff.mul12(abd).cpu().numpy(), oracle.mul12(ab))
+    F = pins.ff_subset()
+    i, j = np.meshgrid(np.arange(F.shape[0]), np.arange(F.shape[0]), indexing="ij")
+    a, b = np.ascontiguousarray(F[i.ravel()]), np.ascontiguousarray(F[j.ravel()])
+    ad, bd = gpu(torch.from_numpy(a)), gpu(torch.from_numpy(b))
+    same_bits(ff.add(ad, bd).cpu().numpy(), oracle.add22(a, b))
+    same_bits(ff.mul(ad, bd).cpu().numpy(), oracle.mul22(a, b))
+    same_bits(ff.div(ad, bd).cpu().numpy(), oracle.div22(a, b))
+    same_bits(ff.add_accurate(ad, bd).cpu().numpy(), oracle.add22_accurate(a, b))
+    s = F.copy()
+    s[s[:, 0] < 0] *= -1
+    same_bits(ff.sqrt(gpu(torch.from_numpy(s))).cpu().numpy(), oracle.sqrt22(s))
+
+
 def _oracle_threaded(fn, *arrays, threads=None):
     """The oracle function over contiguous chunks on all host cores (its C
     loops release the GIL); the result equals one call on the whole arrays."""
