@@ -313,6 +313,22 @@ def test_full_size_sampled_bitexact():
     torch.cuda.empty_cache()
 
 
+def test_mul12_mul22_match_dekker_split_form(cfg0):
+    """The GPU's fused Mul12 against the paper's Split-based (Dekker) form of
+    the oracle: the same pair (RN(ab), ab - RN(ab)) wherever neither part
+    under- or overflows (|a|, |b| in [2^-60, 2^60], |ab| >= 2^-100), up to
+    the sign of a zero error term; likewise Mul22 built on either form."""
+    import test_oracle_pins as pins
+    S = pins.subset_floats()
+    ab = np.concatenate([pins.all_pairs(S), cfg0.ab.numpy()])
+    p = ab[:, 0].astype(np.float64) * ab[:, 1].astype(np.float64)
+    dom = np.all((np.abs(ab) >= 2.0 ** -60) & (np.abs(ab) <= 2.0 ** 60), axis=1) & (np.abs(p) >= 2.0 ** -100)
+    ab = np.ascontiguousarray(ab[dom])
+    pins.assert_same_up_to_zero_sign(ff.mul12(gpu(torch.from_numpy(ab))).cpu().numpy(), oracle.mul12_dekker(ab))
+    a, b = cfg0.a.numpy(), cfg0.b.numpy()
+    pins.assert_same_up_to_zero_sign(ff.mul(gpu(cfg0.a), gpu(cfg0.b)).cpu().numpy(), oracle.mul22_dekker(a, b))
+
+
 def test_bruteforce_subsets_bitexact():
     """Every ordered pair of the oracle pins' brute-force subsets (extreme
     significands 0x800000..0x80000F and 0xFFFFF0..0xFFFFFF, exponents -30..30,
