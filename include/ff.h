@@ -200,9 +200,19 @@ FF_API ff_status ff_reduce2_launch_shape(const float* x, const float* y, size_t 
 /* Float-float GEMV and its adjoint                                          */
 /* ------------------------------------------------------------------------ */
 
-/* Y = A X, Mul22 per term, Add22 accumulation.  A: m x n row-major with row
- * stride lda >= n (elements); X: n x k column-major, column stride ldx >= n;
- * Y: m x k column-major, column stride ldy >= m.  1 <= k <= 64. */
+/* Y = A X with the paper's operators (Section 4.1; the GEMV itself is not in
+ * the paper): every term a Mul22, every accumulation an Add22.  A: m x n
+ * row-major with row stride lda >= n (elements); X: n x k column-major,
+ * column stride ldx >= n; Y: m x k column-major, column stride ldy >= m,
+ * overwritten.  1 <= k <= 64.
+ * Order: row r is reduced by one warp; lane l accumulates, from (0, 0), the
+ * two-value chunks l, l + 32, l + 64, ... of the row in order (the single
+ * values l, l + 32, ... when the row or X is not 16-byte aligned), then the
+ * lanes are combined by a shuffle-down Add22 tree (offsets 16, 8, 4, 2, 1).
+ * The order does not depend on k, so Y is bit-reproducible for any k and
+ * launch.  Error per element: within n 2^-44 sum_j |A[r, j] X[j, c]| of the
+ * exact value (the Add22 and Mul22 bounds of Section 4.1 summed over the
+ * terms). */
 FF_API ff_status ff_gemv(const ff2* A, int64_t m, int64_t n, int64_t lda, const ff2* X, int64_t ldx,
                   int64_t k, ff2* Y, int64_t ldy, cudaStream_t s);
 
@@ -211,8 +221,13 @@ FF_API size_t ff_gemv_t_workspace_bytes(int64_t m, int64_t n, int64_t k);
 
 /* dX = A^T dY (the adjoint of ff_gemv with respect to X).  dY: m x k
  * column-major (stride lddy >= m); dX: n x k column-major (stride
- * lddx >= n).  Row blocks of A are reduced separately into the workspace,
- * then combined in row-block order.  1 <= k <= 64. */
+ * lddx >= n), overwritten.  1 <= k <= 64.
+ * Order: A is cut into row blocks (their number depends on m, n, k and the
+ * device's SM count); within a block each column accumulates its rows in
+ * order with Add22 from (0, 0); the blocks' partial sums go to the workspace
+ * (caller-owned, ff_gemv_t_workspace_bytes, 16-byte aligned) and are added
+ * in row-block order.  Bit-reproducible for a given device and build; error
+ * within m 2^-44 sum_r |A[r, j] dY[r, c]|. */
 FF_API ff_status ff_gemv_t(const ff2* A, int64_t m, int64_t n, int64_t lda, const ff2* dY,
                     int64_t lddy, int64_t k, ff2* dX, int64_t lddx, void* ws, size_t ws_bytes,
                     cudaStream_t s);
