@@ -389,6 +389,18 @@ def test_full_size_every_value_bitexact():
     torch.cuda.empty_cache()
 
 
+@pytest.mark.parametrize("n", [1000, 999])
+def test_gemv_result_does_not_depend_on_k(n):
+    """Every right-hand side is reduced in the same order whatever k and the
+    tile widths are: k = 20 in one call (tiles 16 + 4) equals 20 one-column
+    calls bit for bit, with 16-byte access (n even) and without (n odd)."""
+    gi = inputs.gemv(300, n, 20, inputs.seed_for(4, 95 + n % 2))
+    A, X = gpu(gi.A), gpu(gi.X)
+    Y = ff.gemv(A, X).cpu().numpy()
+    for c in range(20):
+        same_bits(Y[c], ff.gemv(A, X[c:c + 1].contiguous())[0].cpu().numpy())
+
+
 @pytest.mark.parametrize("m,n,k", [(33, 64, 1), (17, 129, 5), (64, 256, 64)])
 def test_gemv_dA_bitexact(m, n, k):
     gi = inputs.gemv(m, n, k, inputs.seed_for(4, 50 + k))
