@@ -232,6 +232,14 @@ FF_API ff_status ff_gemv_t(const ff2* A, int64_t m, int64_t n, int64_t lda, cons
                     int64_t lddy, int64_t k, ff2* dX, int64_t lddx, void* ws, size_t ws_bytes,
                     cudaStream_t s);
 
+/* The row-block count ff_gemv_t uses for these arguments on the current
+ * device, and whether it takes 16-byte access (1) or not (0): the block
+ * b covers rows [b * ceil(m / row_blocks), (b + 1) * ceil(m / row_blocks)).
+ * Lets a test replay the adjoint's order exactly.  Invalid sizes or NULL
+ * outputs return FF_ERR_INVALID_ARG. */
+FF_API ff_status ff_gemv_t_launch_shape(const ff2* A, int64_t m, int64_t n, int64_t lda, int64_t k,
+                                        int64_t* row_blocks, int* vector);
+
 /* Weight gradient of Y = A X: dA = dY X^T, dA[r, j] = sum over c of
  * Mul22(dY[r, c], X[j, c]), accumulated with Add22 in order c = 0 .. k-1
  * (bit-reproducible).  dY: m x k column-major (lddy >= m); X: n x k

@@ -62,6 +62,7 @@ SIGNATURES = {
     "ff_gemv": (ST, [P, I64, I64, I64, P, I64, I64, P, I64, P]),
     "ff_gemv_t_workspace_bytes": (SZ, [I64, I64, I64]),
     "ff_gemv_t": (ST, [P, I64, I64, I64, P, I64, I64, P, I64, P, SZ, P]),
+    "ff_gemv_t_launch_shape": (ST, [P, I64, I64, I64, I64, P, P]),
     "ff_gemv_dA": (ST, [P, I64, I64, P, I64, I64, I64, P, I64, P]),
     "ff_fma_peak": (ST, [ctypes.c_int, I64, ctypes.c_int, ctypes.c_int, P, P]),
     "ff_gemm": (ST, [ctypes.c_int, ctypes.c_int, I64, I64, I64, P, I64, P, I64, P, I64, P]),

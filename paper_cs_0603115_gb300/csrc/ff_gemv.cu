@@ -385,6 +385,19 @@ size_t ff_gemv_t_workspace_bytes(int64_t m, int64_t n, int64_t k)
     return a > b ? a : b;
 }
 
+ff_status ff_gemv_t_launch_shape(const ff2* A, int64_t m, int64_t n, int64_t lda, int64_t k, int64_t* nrb,
+                                 int* vector)
+{
+    if (bad_dims(m, n, k) || lda < n || nrb == nullptr || vector == nullptr) return FF_ERR_INVALID_ARG;
+    ffh::DeviceInfo di;
+    const ff_status st = ffh::device_info(&di);
+    if (st != FF_OK) return st;
+    const bool vec = (n % 2 == 0) && (lda % 2 == 0) && ffh::aligned(A, 16);
+    *nrb = row_blocks(m, n, k, vec, di.sm_count);
+    *vector = vec ? 1 : 0;
+    return FF_OK;
+}
+
 ff_status ff_gemv_t(const ff2* A_, int64_t m, int64_t n, int64_t lda, const ff2* dY_, int64_t lddy, int64_t k,
                     ff2* dX_, int64_t lddx, void* ws, size_t ws_bytes, cudaStream_t s)
 {

@@ -166,3 +166,52 @@ def gemv_rows8_replay(A, x, vec: bool):
         for l in range(off):
             acc[:, l] = add(acc[:, l], acc[:, l + off])
     return acc[:, 0]
+
+
+def gemv_warp_replay(A, X, vec: bool):
+    """ff_gemv's order (include/ff.h): row r is reduced by a warp; lane l
+    accumulates, from (0, 0), its two-value chunks l, l + 32, l + 64, ...
+    (vec) or its values l, l + 32, ... (not vec) with Add22(acc, Mul22(A, X)),
+    then the shuffle-down Add22 tree over offsets 16 .. 1.  A: (m, n, 2);
+    X: (k, n, 2); returns Y as (k, m, 2)."""
+    A = np.ascontiguousarray(A, np.float32)
+    X = np.ascontiguousarray(X, np.float32)
+    m, n = A.shape[0], A.shape[1]
+    k = X.shape[0]
+    Y = np.zeros((k, m, 2), f32)
+    add = lambda a, b: oracle.add22(np.ascontiguousarray(a), np.ascontiguousarray(b))
+    for c in range(k):
+        terms = oracle.mul22(A.reshape(-1, 2), np.tile(X[c], (m, 1))).reshape(m, n, 2) if m * n else np.zeros((m, n, 2), f32)
+        acc = np.zeros((m, 32, 2), f32)
+        for l in range(32):
+            if vec:
+                idx = [j for t in range(l, n // 2, 32) for j in (2 * t, 2 * t + 1)]
+            else:
+                idx = list(range(l, n, 32))
+            for j in idx:
+                acc[:, l] = add(acc[:, l], terms[:, j])
+        for off in (16, 8, 4, 2, 1):
+            for l in range(off):
+                acc[:, l] = add(acc[:, l], acc[:, l + off])
+        Y[c] = acc[:, 0]
+    return Y
+
+
+def gemv_t_replay(A, dY, row_blocks: int):
+    """ff_gemv_t's order (include/ff.h): rows cut into row_blocks blocks of
+    ceil(m / row_blocks) rows; within a block every column accumulates its
+    rows in order from (0, 0) (the oracle's own gemv_t on the block); the
+    blocks' partials are added in block order starting from the first.
+    A: (m, n, 2); dY: (k, m, 2); returns dX as (k, n, 2)."""
+    A = np.ascontiguousarray(A, np.float32)
+    dY = np.ascontiguousarray(dY, np.float32)
+    m = A.shape[0]
+    rpb = -(-m // row_blocks) if m else 0
+    parts = []
+    for b in range(row_blocks):
+        r0, r1 = min(m, b * rpb), min(m, (b + 1) * rpb)
+        parts.append(oracle.gemv_t(np.ascontiguousarray(A[r0:r1]), np.ascontiguousarray(dY[:, r0:r1])))
+    acc = parts[0]
+    for p in parts[1:]:
+        acc = oracle.add22(acc.reshape(-1, 2), p.reshape(-1, 2)).reshape(acc.shape)
+    return acc

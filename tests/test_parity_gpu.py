@@ -389,6 +389,32 @@ def test_full_size_every_value_bitexact():
     torch.cuda.empty_cache()
 
 
+@pytest.mark.parametrize("m,n,k", [(37, 1000, 3), (20, 999, 2), (5, 64, 17), (1, 1, 1), (9, 33, 1)])
+def test_gemv_bitexact_vs_order_replay(m, n, k):
+    """ff_gemv bit for bit against the replay of its documented warp order."""
+    import replay
+    gi = inputs.gemv(m, n, k, inputs.seed_for(4, 120 + n % 7))
+    Y = ff.gemv(gpu(gi.A), gpu(gi.X)).cpu().numpy()
+    same_bits(Y, replay.gemv_warp_replay(gi.A.numpy(), gi.X.numpy(), vec=(n % 2 == 0)))
+
+
+@pytest.mark.parametrize("m,n,k", [(4096, 256, 3), (3000, 130, 2), (70, 513, 5), (31, 8, 1)])
+def test_gemv_t_bitexact_vs_order_replay(m, n, k):
+    """ff_gemv_t bit for bit against the replay of its row-block order (the
+    row-block count read from ff_gemv_t_launch_shape)."""
+    import ctypes
+    import replay
+    gi = inputs.gemv(m, n, k, inputs.seed_for(4, 130 + k))
+    A, dY = gpu(gi.A), gpu(gi.dY)
+    nrb, vec = ctypes.c_int64(), ctypes.c_int()
+    _lib.call("ff_gemv_t_launch_shape", A.data_ptr(), m, n, n, k, ctypes.byref(nrb), ctypes.byref(vec))
+    assert nrb.value >= 1 and bool(vec.value) == (n % 2 == 0)
+    dX = ff.gemv_t(A, dY).cpu().numpy()
+    same_bits(dX, replay.gemv_t_replay(gi.A.numpy(), gi.dY.numpy(), nrb.value))
+    if m >= 4096:
+        assert nrb.value > 1  # the multi-block combine is exercised
+
+
 @pytest.mark.parametrize("n", [1000, 999])
 def test_gemv_result_does_not_depend_on_k(n):
     """Every right-hand side is reduced in the same order whatever k and the
