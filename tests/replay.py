@@ -215,3 +215,71 @@ def gemv_t_replay(A, dY, row_blocks: int):
     for p in parts[1:]:
         acc = oracle.add22(acc.reshape(-1, 2), p.reshape(-1, 2)).reshape(acc.shape)
     return acc
+
+
+def _block_tree(acc, block):
+    """The batched kernel's block reduction: a shuffle-down Add22 tree
+    (offsets 16 .. 1) inside every warp, then warp 0 combines the warps'
+    results (lanes >= warps hold (0, 0)) with offsets warps/2 .. 1."""
+    add = lambda a, b: oracle.add22(np.ascontiguousarray(a), np.ascontiguousarray(b))
+    w = block // 32
+    v = acc.reshape(w, 32, 2).copy()
+    for off in (16, 8, 4, 2, 1):
+        for l in range(off):
+            v[:, l] = add(v[:, l], v[:, l + off])
+    s = v[:, 0].copy()
+    off = w // 2
+    while off > 0:
+        for l in range(off):
+            s[l] = add(s[l:l + 1], s[l + off:l + off + 1])[0]
+        off //= 2
+    return s[0]
+
+
+def batch_dot_replay(x, y, block: int, ppt: int, vec: bool):
+    """A DOT instance of the batched kernel (ff_batch.cu): tiles of
+    block x ppt values; in a tile, thread t accumulates from (0, 0) the
+    two-value chunks t, t + block, ... (vec; with an odd tile length thread 0
+    then adds the last value) or the values t, t + block, ... (not vec), each
+    term Add22(acc, Mul22(x_i, y_i)); the block tree combines the threads;
+    one tile writes its value, several tiles are combined by the last one:
+    thread p adds the tile partials p, p + block, ... from (0, 0), then the
+    block tree.  Returns the (2,) result."""
+    add = lambda a, b: oracle.add22(np.ascontiguousarray(a), np.ascontiguousarray(b))
+    x = np.ascontiguousarray(x, np.float32)
+    y = np.ascontiguousarray(y, np.float32)
+    n = x.shape[0]
+    tile = block * ppt
+    nt = max(1, -(-n // tile))
+    terms = oracle.mul22(x, y) if n else np.zeros((0, 2), f32)
+    parts = []
+    for t in range(nt):
+        s0, s1 = t * tile, min((t + 1) * tile, n)
+        T = terms[s0:s1]
+        ln = s1 - s0
+        acc = np.zeros((block, 2), f32)
+        tid = np.arange(block)
+        if vec:
+            nch = ln // 2
+            for j in range(ppt // 2):
+                c = tid + j * block
+                ok = c < nch
+                if ok.any():
+                    cc = c[ok]
+                    acc[ok] = add(add(acc[ok], T[2 * cc]), T[2 * cc + 1])
+            if ln & 1:
+                acc[0] = add(acc[0:1], T[ln - 1:ln])[0]
+        else:
+            for j in range(ppt):
+                i = tid + j * block
+                ok = i < ln
+                if ok.any():
+                    acc[ok] = add(acc[ok], T[i[ok]])
+        parts.append(_block_tree(acc, block))
+    if nt == 1:
+        return parts[0]
+    P = np.array(parts, f32)
+    acc = np.zeros((block, 2), f32)
+    for p in range(nt):
+        acc[p % block] = add(acc[p % block:p % block + 1], P[p:p + 1])[0]
+    return _block_tree(acc, block)

@@ -232,3 +232,31 @@ def test_batch_gemv_only_plan_bitexact(tune):
             out.fill_(float("nan"))
     plan.close()
 
+
+@pytest.mark.parametrize("tune", [(256, 32, 0, 4), (128, 16, 0, 2), (512, 64, 2, 4), (256, 128, 4, 2)])
+def test_batch_dot_bitexact_vs_order_replay(tune):
+    """DOT instances of a batched plan, aligned (16-byte access) and
+    misaligned, one tile and many: bit for bit against the replay of the
+    kernel's tile, thread and block order for this tune."""
+    from paper_cs_0603115_gb300 import batch
+    import replay
+    lengths = [0, 1, 7, 8191, 8192, 8193, 100001, 33]
+    g = inputs.ill_dot(sum(lengths) + 2 * len(lengths) + 2, 1e8, inputs.seed_for(3, 60))
+    X, Y = g.x.to(DEV), g.y.to(DEV)
+    D = torch.full((len(lengths), 2), float("nan"), device=DEV)
+    specs, keep, o = [], [], 0
+    for i, n in enumerate(lengths):
+        off = o + (i % 2)            # odd instances start 8 bytes past a 16-byte boundary
+        xs, ys = X[off:off + n], Y[off:off + n]
+        specs.append((batch.DOT, xs, ys, D[i], None))
+        keep.append((xs.cpu().numpy(), ys.cpu().numpy(), i % 2 == 0))
+        o = off + n + 2
+        o += o % 2
+    plan = batch.BatchPlan(batch.make_instances(specs), tune=tune)
+    plan.run()
+    torch.cuda.synchronize()
+    got = D.cpu().numpy()
+    for i, (xn, yn, vec) in enumerate(keep):
+        same_bits(got[i], replay.batch_dot_replay(xn, yn, tune[0], tune[1], vec))
+    plan.close()
+
