@@ -133,6 +133,24 @@ gemv_t_kernel(const float2* __restrict__ A, int64_t m, int64_t n, int64_t lda, c
             acc1[c] = make_float2(0.0f, 0.0f);
         }
         int64_t r = r0;
+        if constexpr (KT <= 2) {
+            // four rows loaded ahead of use: a narrow tile has too few terms
+            // per row to hide the HBM latency of the next row's load
+            for (; r + 3 < r1; r += 4) {
+                float4 a[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) a[q] = __ldcs(reinterpret_cast<const float4*>(A + (r + q) * lda) + jp);
+#pragma unroll
+                for (int c = 0; c < KT; ++c) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float2 d = __ldg(dY + c * lddy + r + q);
+                        acc0[c] = ffk::add22(acc0[c], ffk::mul22(make_float2(a[q].x, a[q].y), d));
+                        acc1[c] = ffk::add22(acc1[c], ffk::mul22(make_float2(a[q].z, a[q].w), d));
+                    }
+                }
+            }
+        }
         for (; r + 1 < r1; r += 2) {
             const float4 a0 = __ldcs(reinterpret_cast<const float4*>(A + r * lda) + jp);
             const float4 a1 = __ldcs(reinterpret_cast<const float4*>(A + (r + 1) * lda) + jp);
