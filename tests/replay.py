@@ -217,7 +217,7 @@ def gemv_t_replay(A, dY, row_blocks: int):
     return acc
 
 
-def _block_tree(acc, block):
+def _batch_block_tree(acc, block):
     """The batched kernel's block reduction: a shuffle-down Add22 tree
     (offsets 16 .. 1) inside every warp, then warp 0 combines the warps'
     results (lanes >= warps hold (0, 0)) with offsets warps/2 .. 1."""
@@ -275,11 +275,11 @@ def batch_dot_replay(x, y, block: int, ppt: int, vec: bool):
                 ok = i < ln
                 if ok.any():
                     acc[ok] = add(acc[ok], T[i[ok]])
-        parts.append(_block_tree(acc, block))
+        parts.append(_batch_block_tree(acc, block))
     if nt == 1:
         return parts[0]
     P = np.array(parts, f32)
     acc = np.zeros((block, 2), f32)
     for p in range(nt):
         acc[p % block] = add(acc[p % block:p % block + 1], P[p:p + 1])[0]
-    return _block_tree(acc, block)
+    return _batch_block_tree(acc, block)
