@@ -85,6 +85,31 @@ def test_dot2_sum2_full_size_replay_bitexact():
     same_bits(ff.sum2(g.x).cpu().numpy(), replay.reduce_replay(np.stack([xn, np.zeros_like(xn)], 1), gr, h, v, pol))
 
 
+def test_dot2_sum2_with_specials_follow_the_replay():
+    """Sum2 / Dot2 on binary32 vectors holding infinities, NaN, overflowing
+    products, subnormals and signed zeros: the bits of the replay."""
+    import paper_cs_0603115_gb300 as ff
+    import replay
+    n = 100003
+    g = inputs.ill_dot_f32(n, 1e6, inputs.seed_for(5, 77))
+    x, y = g.x.clone(), g.y.clone()
+    for i, v in {0: float("inf"), 2: -0.0, 5: 1e-42, 999: 3e38, 50000: float("nan"), 50001: -float("inf"),
+                 n - 2: 2.0 ** -149, n - 1: -3e38}.items():
+        x[i] = v
+        y[i] = v if i % 3 else 2.0
+    for drop_nan in (False, True):
+        if drop_nan:
+            x[50000] = 1.0
+        xd, yd = x.to(DEV), y.to(DEV)
+        pol = replay.Dot2Policy()
+        gr, h, v = _shape(xd, yd)
+        want = replay.reduce_replay(oracle.mul12(np.stack([x.numpy(), y.numpy()], 1)), gr, h, v, pol)
+        same_bits(ff.dot2(xd, yd).cpu().numpy(), want)
+        gr, h, v = _shape(xd, None)
+        want = replay.reduce_replay(np.stack([x.numpy(), np.zeros(n, np.float32)], 1), gr, h, v, pol)
+        same_bits(ff.sum2(xd).cpu().numpy(), want)
+
+
 @pytest.mark.parametrize("cond", [1e3, 1e6, 1e9, 1e12])
 def test_dot2_ill_conditioned_within_bound(cond):
     import paper_cs_0603115_gb300 as ff

@@ -181,6 +181,32 @@ def test_dot_and_sum_full_size_replay_bitexact():
     torch.cuda.empty_cache()
 
 
+@pytest.mark.parametrize("offset", [0, 1])
+def test_reductions_with_specials_follow_the_replay(cfg0, offset):
+    """Infinities, NaN, values whose products overflow, subnormals and signed
+    zeros planted at the head, in the middle and at the tail: ff_dot and
+    ff_sum give the bits of the replay of their order (NaN as NaN)."""
+    import replay
+    n = 70001
+    x = cfg0.a[: n + 1].clone()
+    y = cfg0.b[: n + 1].clone()
+    plants = {0: (float("inf"), 0.0), 1: (-0.0, -0.0), 3: (1e-40, 0.0), 4097: (3e38, 1e31),
+              35000: (float("nan"), 0.0), 35001: (-float("inf"), 0.0), n - 1: (2.0 ** -149, 0.0), n: (-3e38, 0.0)}
+    for i, v in plants.items():
+        x[i] = torch.tensor(v)
+        y[i] = torch.tensor((v[0] if i % 2 else 1.5, 0.0))
+    for lo in (0, 1):                       # with and without the NaN
+        xs = gpu(x)[offset:offset + n]
+        ys = gpu(y)[offset:offset + n]
+        if lo:
+            xs = xs.clone(); xs[35000 - offset] = torch.tensor((2.0, 0.0))
+        xn, yn = xs.cpu().numpy(), ys.cpu().numpy()
+        g, h, v = shape_of(xs, ys)
+        same_bits(ff.dot(xs, ys).cpu().numpy(), replay.reduce_replay(oracle.mul22(xn, yn), g, h, v))
+        g, h, v = shape_of(xs, None)
+        same_bits(ff.sum(xs).cpu().numpy(), replay.reduce_replay(xn, g, h, v))
+
+
 def test_dot_mixed_alignment_replay(cfg0):
     n = 70001
     x = gpu(cfg0.a[: n + 1])[:n]
