@@ -45,13 +45,34 @@ def _ptr(t: torch.Tensor) -> int:
     return t.data_ptr()
 
 
-def _check_ff(t: torch.Tensor, name: str) -> None:
+def _check_device(t: torch.Tensor, name: str) -> None:
+    """Kernels launch on the current device with the current stream: every
+    tensor must live there (a tensor of another GPU would be read through a
+    pointer that device cannot use)."""
     if not t.is_cuda:
         raise ValueError(f"{name}: expected a CUDA tensor")
+    cur = torch.cuda.current_device()
+    if t.device.index != cur:
+        raise ValueError(f"{name}: tensor on {t.device} but the current device is cuda:{cur} "
+                         f"(use torch.cuda.device({t.device.index}))")
+
+
+def _check_ff(t: torch.Tensor, name: str) -> None:
+    _check_device(t, name)
     if t.dtype != torch.float32 or t.dim() < 1 or t.shape[-1] != 2:
         raise ValueError(f"{name}: expected float32 with a last dimension of 2, got {t.dtype} {tuple(t.shape)}")
     if not t.is_contiguous():
         raise ValueError(f"{name}: expected a contiguous tensor")
+
+
+def _check_out(t: torch.Tensor, name: str, shape, dtype=torch.float32) -> None:
+    """A caller-supplied output must have exactly the result's shape and
+    dtype, be contiguous and live on the current device: the kernels write
+    through a plain pointer and cannot see its extent."""
+    _check_device(t, name)
+    if t.dtype != dtype or not t.is_contiguous() or tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name}: output must be a contiguous {dtype} tensor of shape {tuple(shape)}, "
+                         f"got {t.dtype} {tuple(t.shape)}{'' if t.is_contiguous() else ' (not contiguous)'}")
 
 
 def _nvals(t: torch.Tensor) -> int:
@@ -152,6 +173,7 @@ def axpy(alpha, x, y, out=None):
         raise ValueError("ff_axpy: shape mismatch")
     if out is None:
         out = torch.empty_like(x)
+    _check_out(out, "ff_axpy", x.shape)
     hi, lo = (float(alpha[0]), float(alpha[1]))
     _lib.call("ff_axpy", ff2(hi, lo), _ptr(x), _ptr(y), _ptr(out), _nvals(x), _stream())
     return out
@@ -169,6 +191,7 @@ def sum(x, out=None):  # noqa: A001  (mirrors the C name ff_sum)
     _check_ff(x, "ff_sum")
     if out is None:
         out = torch.empty(2, dtype=torch.float32, device=x.device)
+    _check_out(out, "ff_sum", (2,))
     n = _nvals(x)
     ws = _reduce_ws(n, x.device)
     _lib.call("ff_sum", _ptr(x), n, _ptr(out), _ptr(ws), ws.numel(), _stream())
@@ -183,6 +206,7 @@ def dot(x, y, out=None):
         raise ValueError("ff_dot: shape mismatch")
     if out is None:
         out = torch.empty(2, dtype=torch.float32, device=x.device)
+    _check_out(out, "ff_dot", (2,))
     n = _nvals(x)
     ws = _reduce_ws(n, x.device)
     _lib.call("ff_dot", _ptr(x), _ptr(y), n, _ptr(out), _ptr(ws), ws.numel(), _stream())
@@ -190,7 +214,8 @@ def dot(x, y, out=None):
 
 
 def _f32_vec(t, name):
-    if not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+    _check_device(t, name)
+    if t.dtype != torch.float32 or not t.is_contiguous():
         raise ValueError(f"{name}: expected a contiguous float32 CUDA tensor")
 
 
@@ -200,6 +225,7 @@ def sum2(x, out=None):
     _f32_vec(x, "ff_sum2")
     if out is None:
         out = torch.empty(2, dtype=torch.float32, device=x.device)
+    _check_out(out, "ff_sum2", (2,))
     ws = _reduce_ws(x.numel(), x.device)
     _lib.call("ff_sum2", _ptr(x), x.numel(), _ptr(out), _ptr(ws), ws.numel(), _stream())
     return out
@@ -214,6 +240,7 @@ def dot2(x, y, out=None):
         raise ValueError("ff_dot2: size mismatch")
     if out is None:
         out = torch.empty(2, dtype=torch.float32, device=x.device)
+    _check_out(out, "ff_dot2", (2,))
     ws = _reduce_ws(x.numel(), x.device)
     _lib.call("ff_dot2", _ptr(x), _ptr(y), x.numel(), _ptr(out), _ptr(ws), ws.numel(), _stream())
     return out
@@ -224,10 +251,14 @@ def dot_backward(dout, x, y, dx=None, dy=None):
     _check_ff(dout, "ff_dot_backward")
     _check_ff(x, "ff_dot_backward")
     _check_ff(y, "ff_dot_backward")
+    if dout.numel() != 2 or x.shape != y.shape:
+        raise ValueError("ff_dot_backward: expected dout of 2 values and x, y of one shape")
     if dx is None:
         dx = torch.empty_like(x)
     if dy is None:
         dy = torch.empty_like(y)
+    _check_out(dx, "ff_dot_backward", x.shape)
+    _check_out(dy, "ff_dot_backward", y.shape)
     _lib.call("ff_dot_backward", _ptr(dout), _ptr(x), _ptr(y), _ptr(dx), _ptr(dy), _nvals(x), _stream())
     return dx, dy
 
@@ -246,6 +277,7 @@ def gemv(A, X, out=None):
     k = X.shape[0]
     if out is None:
         out = torch.empty((k, m, 2), dtype=torch.float32, device=A.device)
+    _check_out(out, "ff_gemv", (k, m, 2))
     _lib.call("ff_gemv", _ptr(A), m, n, n, _ptr(X), n, k, _ptr(out), m, _stream())
     return out
 
@@ -260,6 +292,7 @@ def gemv_t(A, dY, out=None):
     k = dY.shape[0]
     if out is None:
         out = torch.empty((k, n, 2), dtype=torch.float32, device=A.device)
+    _check_out(out, "ff_gemv_t", (k, n, 2))
     nbytes = _lib.load().ff_gemv_t_workspace_bytes(m, n, k)
     ws = workspace(nbytes, A.device, key="gemv_t")
     _lib.call("ff_gemv_t", _ptr(A), m, n, n, _ptr(dY), m, k, _ptr(out), n, _ptr(ws), ws.numel(), _stream())
@@ -277,6 +310,7 @@ def gemv_dA(dY, X, out=None):
     n = X.shape[1]
     if out is None:
         out = torch.empty((m, n, 2), dtype=torch.float32, device=dY.device)
+    _check_out(out, "ff_gemv_dA", (m, n, 2))
     _lib.call("ff_gemv_dA", _ptr(dY), m, m, _ptr(X), n, n, k, _ptr(out), n, _stream())
     return out
 
@@ -295,6 +329,7 @@ def gemm(A, B, transa=False, transb=False, out=None):
         raise ValueError(f"ff_gemm: inner dimensions differ ({k} and {kb})")
     if out is None:
         out = torch.empty((m, n, 2), dtype=torch.float32, device=A.device)
+    _check_out(out, "ff_gemm", (m, n, 2))
     _lib.call("ff_gemm", int(bool(transa)), int(bool(transb)), m, n, k, _ptr(A), max(A.shape[1], 1), _ptr(B),
               max(B.shape[1], 1), _ptr(out), max(n, 1), _stream())
     return out
@@ -374,14 +409,18 @@ def ffgemm(A, B):
 # native baselines
 # ---------------------------------------------------------------------------
 def _f64_check(t, name):
-    if not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+    _check_device(t, name)
+    if t.dtype != torch.float64 or not t.is_contiguous():
         raise ValueError(f"{name}: expected a contiguous float64 CUDA tensor")
 
 
 def _f64_binary(name, a, b, out):
     _f64_check(a, name)
     _f64_check(b, name)
+    if a.shape != b.shape:
+        raise ValueError(f"{name}: shape mismatch")
     out = torch.empty_like(a) if out is None else out
+    _check_out(out, name, a.shape, torch.float64)
     _lib.call(name, _ptr(a), _ptr(b), _ptr(out), a.numel(), _stream())
     return out
 
@@ -394,6 +433,7 @@ def f64_div(a, b, out=None): return _f64_binary("ff_f64_div", a, b, out)
 def f64_sqrt(a, out=None):
     _f64_check(a, "ff_f64_sqrt")
     out = torch.empty_like(a) if out is None else out
+    _check_out(out, "ff_f64_sqrt", a.shape, torch.float64)
     _lib.call("ff_f64_sqrt", _ptr(a), _ptr(out), a.numel(), _stream())
     return out
 
@@ -401,7 +441,10 @@ def f64_sqrt(a, out=None):
 def f64_dot(x, y, out=None):
     _f64_check(x, "ff_f64_dot")
     _f64_check(y, "ff_f64_dot")
+    if x.shape != y.shape:
+        raise ValueError("ff_f64_dot: shape mismatch")
     out = torch.empty(1, dtype=torch.float64, device=x.device) if out is None else out
+    _check_out(out, "ff_f64_dot", (1,), torch.float64)
     ws = _reduce_ws(x.numel(), x.device)
     _lib.call("ff_f64_dot", _ptr(x), _ptr(y), x.numel(), _ptr(out), _ptr(ws), ws.numel(), _stream())
     return out
@@ -411,28 +454,38 @@ def f64_gemv(A, X, out=None):
     """Binary64 Y = A X; A (m, n), X (k, n); returns (k, m)."""
     _f64_check(A, "ff_f64_gemv")
     _f64_check(X, "ff_f64_gemv")
+    if A.dim() != 2 or X.dim() != 2 or X.shape[1] != A.shape[1]:
+        raise ValueError("ff_f64_gemv: expected A (m, n) and X (k, n)")
     m, n = A.shape
     k = X.shape[0]
     out = torch.empty((k, m), dtype=torch.float64, device=A.device) if out is None else out
+    _check_out(out, "ff_f64_gemv", (k, m), torch.float64)
     _lib.call("ff_f64_gemv", _ptr(A), m, n, n, _ptr(X), n, k, _ptr(out), m, _stream())
     return out
 
 
 def _f32_check(t, name):
-    if not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+    _check_device(t, name)
+    if t.dtype != torch.float32 or not t.is_contiguous():
         raise ValueError(f"{name}: expected a contiguous float32 CUDA tensor")
 
 
 def f32_add(a, b, out=None):
     _f32_check(a, "ff_f32_add"); _f32_check(b, "ff_f32_add")
+    if a.shape != b.shape:
+        raise ValueError("ff_f32_add: shape mismatch")
     out = torch.empty_like(a) if out is None else out
+    _check_out(out, "ff_f32_add", a.shape)
     _lib.call("ff_f32_add", _ptr(a), _ptr(b), _ptr(out), a.numel(), _stream())
     return out
 
 
 def f32_mul(a, b, out=None):
     _f32_check(a, "ff_f32_mul"); _f32_check(b, "ff_f32_mul")
+    if a.shape != b.shape:
+        raise ValueError("ff_f32_mul: shape mismatch")
     out = torch.empty_like(a) if out is None else out
+    _check_out(out, "ff_f32_mul", a.shape)
     _lib.call("ff_f32_mul", _ptr(a), _ptr(b), _ptr(out), a.numel(), _stream())
     return out
 
@@ -440,7 +493,10 @@ def f32_mul(a, b, out=None):
 def f32_mad(a, b, c, out=None):
     for t in (a, b, c):
         _f32_check(t, "ff_f32_mad")
+    if a.shape != b.shape or a.shape != c.shape:
+        raise ValueError("ff_f32_mad: shape mismatch")
     out = torch.empty_like(a) if out is None else out
+    _check_out(out, "ff_f32_mad", a.shape)
     _lib.call("ff_f32_mad", _ptr(a), _ptr(b), _ptr(c), _ptr(out), a.numel(), _stream())
     return out
 
@@ -451,5 +507,6 @@ def fma_peak(f64: bool, iters: int, blocks: int, threads: int = 256, device=None
     dtype = torch.float64 if f64 else torch.float32
     if out is None:
         out = torch.empty(blocks * threads, dtype=dtype, device=device or "cuda")
+    _check_out(out, "ff_fma_peak", (blocks * threads,), dtype)
     _lib.call("ff_fma_peak", int(bool(f64)), iters, blocks, threads, _ptr(out), _stream())
     return out

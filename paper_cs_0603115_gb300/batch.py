@@ -26,6 +26,28 @@ GEMV = 3
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "ff_gb300", "autotune.json")
 
 
+def _check_instance(i, kind, x, y, out, out2, dout, cur):
+    """The plan reads and writes through plain pointers: every tensor must be
+    a contiguous float32 tensor on the current device with the extent the
+    instance kind implies."""
+    def ok(t, numel=None):
+        return (t is not None and t.is_cuda and t.device.index == cur and t.dtype == torch.float32
+                and t.is_contiguous() and (numel is None or t.numel() == numel))
+    if kind == GEMV:
+        good = (ok(x) and x.dim() == 3 and x.shape[2] == 2 and ok(y, 2 * x.shape[1]) and ok(out, 2 * x.shape[0]))
+    elif kind == DOT:
+        good = ok(x) and ok(y, x.numel()) and ok(out, 2)
+    elif kind == AXPY:
+        good = ok(x) and ok(y, x.numel()) and ok(out, x.numel())
+    elif kind == DOT_GRAD:
+        good = ok(x) and ok(y, x.numel()) and ok(out, x.numel()) and ok(out2, x.numel()) and ok(dout, 2)
+    else:
+        raise ValueError(f"instance {i}: unknown kind {kind}")
+    if not good:
+        raise ValueError(f"instance {i} (kind {kind}): tensors must be contiguous float32 on cuda:{cur} "
+                         "with the sizes of that kind")
+
+
 def make_instances(specs) -> ctypes.Array:
     """specs: iterable of (kind, x, y, out, alpha) or (kind, x, y, out, alpha,
     out2, dout) with x, y, out CUDA float-float tensors (out is a (2,) tensor
@@ -34,10 +56,12 @@ def make_instances(specs) -> ctypes.Array:
     row-major matrix, y the (n, 2) vector and out the (m, 2) result."""
     specs = list(specs)
     arr = (ff_batch_instance * len(specs))()
+    cur = torch.cuda.current_device()
     for i, spec in enumerate(specs):
         kind, x, y, out, alpha = spec[:5]
         out2 = spec[5] if len(spec) > 5 else None
         dout = spec[6] if len(spec) > 6 else None
+        _check_instance(i, kind, x, y, out, out2, dout, cur)
         arr[i].kind = kind
         arr[i].reserved = 0
         if kind == GEMV:

@@ -154,7 +154,10 @@ def test_batch_errors():
     out = torch.zeros((10, 2), device=DEV)
     inst = batch.make_instances([(batch.AXPY, x, x, out, (1.0, 0.0))])
     L = _lib.load()
-    bad = batch.make_instances([(7, x, x, out, None)])
+    with pytest.raises(ValueError):                 # the wrapper refuses an unknown kind
+        batch.make_instances([(7, x, x, out, None)])
+    bad = batch.make_instances([(batch.AXPY, x, x, out, (1.0, 0.0))])
+    bad[0].kind = 7                                 # and so does the C ABI, given the raw record
     h = ctypes.c_void_p()
     assert L.ff_batch_plan_create(bad, 1, None, ctypes.byref(h)) == 1
     t = _lib.ff_tune(256, 3, 0)     # unsupported pairs_per_thread
