@@ -314,6 +314,26 @@ def test_f64_and_f32_baselines(cfg0):
     torch.testing.assert_close(Y, X64 @ A64.T, rtol=1e-13, atol=0)
 
 
+def test_gemv_and_f64_gemv_normwise_2m44():
+    """The float-float GEMV and the binary64 baseline GEMV at the benchmark's
+    row width (32768): every element within 2^-44 sum_j |A_rj x_j| of the
+    exact value (superaccumulator), the per-row normwise reading of a
+    relative error <= 2^-44."""
+    m, n, k = 48, 32768, 4
+    gi = inputs.gemv(m, n, k, inputs.seed_for(4, 150))
+    A, X = gi.A.numpy(), gi.X.numpy()
+    Y = ff.gemv(gpu(gi.A), gpu(gi.X)).cpu().numpy()
+    Y64 = ff.f64_gemv(inputs.ff_to_f64(gi.A).to(DEV), inputs.ff_to_f64(gi.X).to(DEV)).cpu().numpy()
+    worst = worst64 = 0.0
+    for c in range(k):
+        for r in range(m):
+            s_hi, s_lo, Aabs, E = oracle.exact_dot(A[r], X[c], Y[c, r])
+            worst = max(worst, abs(E) / Aabs)
+            e64 = abs((Y64[c, r] - s_hi) - s_lo)   # binary128 exact value as a double pair
+            worst64 = max(worst64, e64 / Aabs)
+    assert worst <= 2.0 ** -44 and worst64 <= 2.0 ** -44, (worst, worst64)
+
+
 # ---------------------------------------------------------------------------
 # full size (2^28 values), sampled against the oracle
 # ---------------------------------------------------------------------------
