@@ -412,8 +412,10 @@ def run_gpu(args):
         del host_in, host_out, dev_in
         torch.cuda.synchronize()
 
+    # the oracle on the host cores: rank 0 of a one-GPU run only (with more
+    # ranks the other processes would share the cores it is timed on)
     cpu = None
-    if rank == 0 and not args.no_cpu:
+    if rank == 0 and ws == 1 and not args.no_cpu:
         cpu = cpu_baseline(e)
 
     if args.rows == "all":
