@@ -58,6 +58,17 @@ def test_gemm_transposes_bitexact(m, n, k, transa, transb):
     same_bits(C, oracle.gemm(A.numpy(), B.numpy(), transa=bool(transa), transb=bool(transb)))
 
 
+@pytest.mark.parametrize("transa,transb", [(0, 0), (1, 0), (0, 1), (1, 1)])
+def test_gemm_many_ragged_tiles_bitexact(transa, transb):
+    """1285 x 1097 (ragged in both directions): 21 x 18 = 378 tiles, more
+    than one wave of resident blocks, every element equal to the oracle's
+    in-order loop."""
+    m, n, k = 1285, 1097, 24
+    A, B = operands(m, n, k, inputs.seed_for(6, 50 + transa + 2 * transb), bool(transa), bool(transb))
+    C = ff.gemm(A.to(DEV), B.to(DEV), transa=bool(transa), transb=bool(transb)).cpu().numpy()
+    same_bits(C, oracle.gemm(A.numpy(), B.numpy(), transa=bool(transa), transb=bool(transb)))
+
+
 def test_gemm_padded_leading_dimensions_and_guards():
     """lda, ldb, ldc larger than the rows; nothing outside C's m x n block
     (the padding columns and the rows around it) is written."""
