@@ -445,6 +445,10 @@ def extra_rows(torch, ff, inputs, e, dev, peaks):
     out = {}
     hbm = peaks["hbm_gbs"]
     n = e.a.shape[0]
+    # the measured FP32 / FP64 peaks first: the FP32-bound rows divide by them
+    alu = alu_peaks(torch, ff, dev)
+    out["alu_peaks"] = alu
+    fp32 = alu["f32_fma_lane_ops_s"]
     # native baselines on the same values (FP64 holds hi + lo exactly)
     a64 = inputs.ff_to_f64(e.a)
     b64 = inputs.ff_to_f64(e.b)
@@ -542,8 +546,11 @@ def extra_rows(torch, ff, inputs, e, dev, peaks):
         tb = time_fn(torch, lambda: ff.gemv_t(A, X), 2, warm=1)
         tot_f += tf
         tot_b += tb
+        t_bound = max(8 * M * N / (hbm * 1e9), 28 * M * N * k / fp32)   # roofline time of one call
         gem[str(k)] = {"fwd_ms": round(tf * 1e3, 3), "adj_ms": round(tb * 1e3, 3),
-                       "fwd_ff_op_s": 2 * M * N * k / tf, "adj_ff_op_s": 2 * M * N * k / tb}
+                       "fwd_ff_op_s": 2 * M * N * k / tf, "adj_ff_op_s": 2 * M * N * k / tb,
+                       "bound": "hbm" if 8 * M * N / (hbm * 1e9) >= 28 * M * N * k / fp32 else "fp32",
+                       "fwd_frac_roofline": round(t_bound / tf, 4), "adj_frac_roofline": round(t_bound / tb, 4)}
     out["gemv_32768^2"] = {"per_k": gem, "sweep_fwd_ms": round(tot_f * 1e3, 2), "sweep_adj_ms": round(tot_b * 1e3, 2),
                            "k1_fwd_GB/s": round(8 * M * N / (gem["1"]["fwd_ms"] / 1e3) / 1e9, 1)}
     A64 = inputs.ff_to_f64(A)
@@ -559,8 +566,6 @@ def extra_rows(torch, ff, inputs, e, dev, peaks):
     del A64, X64, Xall
     torch.cuda.empty_cache()
     out.update(batched_rows(torch, ff, inputs, dev, peaks))
-    alu = alu_peaks(torch, ff, dev)
-    out["alu_peaks"] = alu
     out.update(gemm_rows(torch, ff, inputs, dev, fp32_measured=alu["f32_fma_lane_ops_s"]))
     return out
 
