@@ -133,9 +133,10 @@ gemv_t_kernel(const float2* __restrict__ A, int64_t m, int64_t n, int64_t lda, c
             acc1[c] = make_float2(0.0f, 0.0f);
         }
         int64_t r = r0;
-        if constexpr (KT <= 2) {
+        if constexpr (KT <= 7) {
             // four rows loaded ahead of use: a narrow tile has too few terms
-            // per row to hide the HBM latency of the next row's load
+            // per row to hide the HBM latency of the next row's load (from
+            // eight right-hand sides on, two rows measured faster)
             for (; r + 3 < r1; r += 4) {
                 float4 a[4];
 #pragma unroll
