@@ -540,17 +540,21 @@ def extra_rows(torch, ff, inputs, e, dev, peaks):
                                               dev)).reshape(64, N, 2)
     gem = {}
     tot_f = tot_b = 0.0
+    dA = torch.empty_like(A)   # the weight gradient dY X^T: one write of every A value
     for k in ks:
         X = Xall[:k].contiguous()
         tf = time_fn(torch, lambda: ff.gemv(A, X), 2, warm=1)
         tb = time_fn(torch, lambda: ff.gemv_t(A, X), 2, warm=1)
+        tw = time_fn(torch, lambda: ff.gemv_dA(X, X, out=dA), 2, warm=1)
         tot_f += tf
         tot_b += tb
         t_bound = max(8 * M * N / (hbm * 1e9), 28 * M * N * k / fp32)   # roofline time of one call
-        gem[str(k)] = {"fwd_ms": round(tf * 1e3, 3), "adj_ms": round(tb * 1e3, 3),
+        gem[str(k)] = {"fwd_ms": round(tf * 1e3, 3), "adj_ms": round(tb * 1e3, 3), "dA_ms": round(tw * 1e3, 3),
                        "fwd_ff_op_s": 2 * M * N * k / tf, "adj_ff_op_s": 2 * M * N * k / tb,
                        "bound": "hbm" if 8 * M * N / (hbm * 1e9) >= 28 * M * N * k / fp32 else "fp32",
-                       "fwd_frac_roofline": round(t_bound / tf, 4), "adj_frac_roofline": round(t_bound / tb, 4)}
+                       "fwd_frac_roofline": round(t_bound / tf, 4), "adj_frac_roofline": round(t_bound / tb, 4),
+                       "dA_frac_roofline": round(t_bound / tw, 4)}
+    del dA
     out["gemv_32768^2"] = {"per_k": gem, "sweep_fwd_ms": round(tot_f * 1e3, 2), "sweep_adj_ms": round(tot_b * 1e3, 2),
                            "k1_fwd_GB/s": round(8 * M * N / (gem["1"]["fwd_ms"] / 1e3) / 1e9, 1)}
     A64 = inputs.ff_to_f64(A)

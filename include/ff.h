@@ -243,8 +243,9 @@ FF_API ff_status ff_gemv_t_launch_shape(const ff2* A, int64_t m, int64_t n, int6
 /* Weight gradient of Y = A X: dA = dY X^T, dA[r, j] = sum over c of
  * Mul22(dY[r, c], X[j, c]), accumulated with Add22 in order c = 0 .. k-1
  * (bit-reproducible).  dY: m x k column-major (lddy >= m); X: n x k
- * column-major (ldx >= n); dA: m x n row-major (ldda >= n), overwritten.
- * 1 <= k <= 64. */
+ * column-major (ldx >= n); dA: m x n row-major (ldda >= n), overwritten;
+ * it must not overlap dY or X.  1 <= k <= 64.  From k = 5 on the call runs
+ * ff_gemm (transa = 1 on dY), which forms the same terms in the same order. */
 FF_API ff_status ff_gemv_dA(const ff2* dY, int64_t m, int64_t lddy, const ff2* X, int64_t n, int64_t ldx,
                             int64_t k, ff2* dA, int64_t ldda, cudaStream_t s);
 

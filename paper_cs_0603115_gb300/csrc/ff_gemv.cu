@@ -280,38 +280,69 @@ int64_t row_blocks(int64_t m, int64_t n, int64_t k, bool vec, int sm_count)
 }
 
 // ---------------------------------------------------------------------------
-// dA = dY X^T: one thread per pair of adjacent columns j of one row r of dA
-// (coalesced 16-byte loads of X and stores of dA along the row); the k terms
-// of each element are accumulated in order c = 0 .. k-1, so the result is
-// the oracle's left-to-right sum bit for bit.  dY[r, c] is a warp-uniform
-// broadcast load.
+// dA = dY X^T.  Every element accumulates its k terms Mul22(dY[r, c], X[j, c])
+// in order c = 0 .. k-1 from (0, 0), so the result is the oracle's
+// left-to-right sum bit for bit.  k > 4 runs as the matrix product
+// op(dY) X on the GEMM kernel (the same terms in the same order); k <= 4 runs
+// here: one thread per pair of adjacent columns (16-byte access) or per
+// column, rows walked by a grid of about one wave of blocks.
 // ---------------------------------------------------------------------------
-template <bool VEC>
 __global__ void __launch_bounds__(kGBlock)
-gemv_dA_kernel(const float2* __restrict__ dY, int64_t m, int64_t lddy, const float2* __restrict__ X, int64_t n,
-               int64_t ldx, int64_t k, float2* __restrict__ dA, int64_t ldda)
+gemv_dA_scalar_kernel(const float2* __restrict__ dY, int64_t m, int64_t lddy, const float2* __restrict__ X,
+                      int64_t n, int64_t ldx, int64_t k, float2* __restrict__ dA, int64_t ldda)
 {
-    // rows r = blockIdx.y, blockIdx.y + gridDim.y, ... (gridDim.y <= 65535)
+    const int64_t j = static_cast<int64_t>(blockIdx.x) * kGBlock + threadIdx.x;
+    if (j >= n) return;
     for (int64_t r = blockIdx.y; r < m; r += gridDim.y) {
-        if (VEC) {
-            const int64_t jp = static_cast<int64_t>(blockIdx.x) * kGBlock + threadIdx.x;
-            if (2 * jp >= n) return;
-            float2 acc0 = make_float2(0.0f, 0.0f), acc1 = make_float2(0.0f, 0.0f);
-            for (int64_t c = 0; c < k; ++c) {
-                const float2 d = __ldg(dY + c * lddy + r);
-                const float4 x = __ldg(reinterpret_cast<const float4*>(X + c * ldx) + jp);
-                acc0 = ffk::add22(acc0, ffk::mul22(d, make_float2(x.x, x.y)));
-                acc1 = ffk::add22(acc1, ffk::mul22(d, make_float2(x.z, x.w)));
-            }
-            __stcs(reinterpret_cast<float4*>(dA + r * ldda) + jp, make_float4(acc0.x, acc0.y, acc1.x, acc1.y));
-        } else {
-            const int64_t j = static_cast<int64_t>(blockIdx.x) * kGBlock + threadIdx.x;
-            if (j >= n) return;
-            float2 acc = make_float2(0.0f, 0.0f);
-            for (int64_t c = 0; c < k; ++c)
-                acc = ffk::add22(acc, ffk::mul22(__ldg(dY + c * lddy + r), X[c * ldx + j]));
-            dA[r * ldda + j] = acc;
+        float2 acc = make_float2(0.0f, 0.0f);
+        for (int64_t c = 0; c < k; ++c) acc = ffk::add22(acc, ffk::mul22(__ldg(dY + c * lddy + r), X[c * ldx + j]));
+        dA[r * ldda + j] = acc;
+    }
+}
+
+// dA for k <= 4 with 16-byte access: the thread's k column-pair values of X
+// stay in registers, and each row pair's 2k values of dY are loaded before
+// any is used; same per-element order (c = 0 .. k-1 from (0, 0)).
+template <int KT>
+__global__ void __launch_bounds__(kGBlock)
+gemv_dA_small_kernel(const float2* __restrict__ dY, int64_t m, int64_t lddy, const float2* __restrict__ X, int64_t n,
+                     int64_t ldx, float2* __restrict__ dA, int64_t ldda)
+{
+    const int64_t gy = gridDim.y;
+    const int64_t jp = static_cast<int64_t>(blockIdx.x) * kGBlock + threadIdx.x;
+    if (2 * jp >= n) return;
+    float4 x[KT];
+#pragma unroll
+    for (int c = 0; c < KT; ++c) x[c] = __ldg(reinterpret_cast<const float4*>(X + c * ldx) + jp);
+    int64_t r = blockIdx.y;
+    for (; r + gy < m; r += 2 * gy) {
+        const int64_t r1 = r + gy;
+        float2 d0[KT], d1[KT];
+#pragma unroll
+        for (int c = 0; c < KT; ++c) {
+            d0[c] = __ldg(dY + c * lddy + r);
+            d1[c] = __ldg(dY + c * lddy + r1);
         }
+        float2 a00 = make_float2(0.0f, 0.0f), a01 = a00, a10 = a00, a11 = a00;
+#pragma unroll
+        for (int c = 0; c < KT; ++c) {
+            a00 = ffk::add22(a00, ffk::mul22(d0[c], make_float2(x[c].x, x[c].y)));
+            a01 = ffk::add22(a01, ffk::mul22(d0[c], make_float2(x[c].z, x[c].w)));
+            a10 = ffk::add22(a10, ffk::mul22(d1[c], make_float2(x[c].x, x[c].y)));
+            a11 = ffk::add22(a11, ffk::mul22(d1[c], make_float2(x[c].z, x[c].w)));
+        }
+        __stcs(reinterpret_cast<float4*>(dA + r * ldda) + jp, make_float4(a00.x, a00.y, a01.x, a01.y));
+        __stcs(reinterpret_cast<float4*>(dA + r1 * ldda) + jp, make_float4(a10.x, a10.y, a11.x, a11.y));
+    }
+    if (r < m) {
+        float2 a0 = make_float2(0.0f, 0.0f), a1 = a0;
+#pragma unroll
+        for (int c = 0; c < KT; ++c) {
+            const float2 d = __ldg(dY + c * lddy + r);
+            a0 = ffk::add22(a0, ffk::mul22(d, make_float2(x[c].x, x[c].y)));
+            a1 = ffk::add22(a1, ffk::mul22(d, make_float2(x[c].z, x[c].w)));
+        }
+        __stcs(reinterpret_cast<float4*>(dA + r * ldda) + jp, make_float4(a0.x, a0.y, a1.x, a1.y));
     }
 }
 
@@ -481,17 +512,40 @@ ff_status ff_gemv_dA(const ff2* dY_, int64_t m, int64_t lddy, const ff2* X_, int
     if (!ffh::ok_ptr(dY_, static_cast<size_t>(m)) || !ffh::ok_ptr(X_, static_cast<size_t>(n)) || !ffh::ok_ptr(dA_, an))
         return FF_ERR_INVALID_ARG;
     if (m == 0 || n == 0) return FF_OK;
+    // from five right-hand sides on, dA is a matrix product op(dY) X with dY
+    // read transposed in place: the GEMM kernel computes every element with
+    // the same Mul22(dY[r, c], X[j, c]) terms in the same order (bit-identical)
+    // at its higher arithmetic rate
+    if (k > 4) return ff_gemm(1, 0, m, n, k, dY_, lddy, X_, ldx, dA_, ldda, s);
     auto* dY = reinterpret_cast<const float2*>(dY_);
     auto* X = reinterpret_cast<const float2*>(X_);
     auto* dA = reinterpret_cast<float2*>(dA_);
     const bool vec = (n % 2 == 0) && (ldx % 2 == 0) && (ldda % 2 == 0) && ffh::aligned(X, 16) && ffh::aligned(dA, 16);
-    const unsigned gy = static_cast<unsigned>(m < 65535 ? m : 65535);
+    ffh::DeviceInfo di;
+    const ff_status st = ffh::device_info(&di);
+    if (st != FF_OK) return st;
+    // one wave of resident blocks (rounded down so that every block is
+    // resident at once: all walk the same number of rows); every block walks
+    // rows blockIdx.y, blockIdx.y + gridDim.y, ...
+    const int64_t col_blocks = ((vec ? n / 2 : n) + kGBlock - 1) / kGBlock;
+    const int occ = ffh::occupancy(vec ? reinterpret_cast<const void*>(&gemv_dA_small_kernel<4>)
+                                       : reinterpret_cast<const void*>(&gemv_dA_scalar_kernel), kGBlock);
+    int64_t gy64 = static_cast<int64_t>(di.sm_count) * (occ > 0 ? occ : 1) / col_blocks;
+    if (gy64 > m) gy64 = m;
+    if (gy64 > 65535) gy64 = 65535;
+    if (gy64 < 1) gy64 = 1;
+    const unsigned gy = static_cast<unsigned>(gy64);
     if (vec) {
         dim3 grid(static_cast<unsigned>((n / 2 + kGBlock - 1) / kGBlock), gy);
-        gemv_dA_kernel<true><<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, k, dA, ldda);
+        switch (k) {
+        case 1: gemv_dA_small_kernel<1><<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, dA, ldda); break;
+        case 2: gemv_dA_small_kernel<2><<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, dA, ldda); break;
+        case 3: gemv_dA_small_kernel<3><<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, dA, ldda); break;
+        default: gemv_dA_small_kernel<4><<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, dA, ldda); break;
+        }
     } else {
         dim3 grid(static_cast<unsigned>((n + kGBlock - 1) / kGBlock), gy);
-        gemv_dA_kernel<false><<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, k, dA, ldda);
+        gemv_dA_scalar_kernel<<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, k, dA, ldda);
     }
     return ffh::check_launch();
 }
