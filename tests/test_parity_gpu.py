@@ -473,7 +473,8 @@ def test_gemv_result_does_not_depend_on_k(n):
         same_bits(Y[c], ff.gemv(A, X[c:c + 1].contiguous())[0].cpu().numpy())
 
 
-@pytest.mark.parametrize("m,n,k", [(33, 64, 1), (17, 129, 5), (64, 256, 64)])
+@pytest.mark.parametrize("m,n,k", [(33, 64, 1), (17, 129, 5), (64, 256, 64), (17, 129, 3), (301, 1000, 4),
+                                   (300, 998, 2)])
 def test_gemv_dA_bitexact(m, n, k):
     gi = inputs.gemv(m, n, k, inputs.seed_for(4, 50 + k))
     dA = ff.gemv_dA(gpu(gi.dY), gpu(gi.X)).cpu().numpy()
