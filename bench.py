@@ -474,6 +474,11 @@ def extra_rows(torch, ff, inputs, e, dev, peaks):
     t = time_fn(torch, lambda: ff.add_accurate(e.a, e.b, out=oacc), 5)
     out["add_accurate"] = {"ms": round(t * 1e3, 4), "GB/s": round(24 * n / t / 1e9, 1),
                            "frac_hbm": round(24 * n / t / 1e9 / hbm, 4), "ff_op_s": n / t}
+    # AXPY z = Add22(Mul22(alpha, x), y) on the same operands (24 B per value, 2 ff-ops)
+    alpha = tuple(float(v) for v in inputs.scalar_ff(inputs.seed_for(1, 5)))
+    t = time_fn(torch, lambda: ff.axpy(alpha, e.a, e.b, out=oacc), 5)
+    out["axpy"] = {"ms": round(t * 1e3, 4), "GB/s": round(24 * n / t / 1e9, 1),
+                   "frac_hbm": round(24 * n / t / 1e9 / hbm, 4), "ff_op_s": 2 * n / t}
     del oacc
     torch.cuda.empty_cache()
     # the reductions at the elementwise size (2^28 values of the same arrays):
