@@ -26,7 +26,7 @@ from ._lib import FFError, ff2
 __all__ = [
     "add12", "mul12", "add", "add_accurate", "sum2", "dot2", "mul", "div", "sqrt", "axpy", "sum", "dot", "dot_backward",
     "gemv", "gemv_t", "gemv_dA", "gemm", "FFDot", "FFGemv", "FFGemm", "ffdot", "ffgemv", "ffgemm", "FFError",
-    "workspace",
+    "workspace", "clear_workspaces",
     "f64_add", "f64_mul", "f64_div", "f64_sqrt", "f64_dot", "f64_gemv", "f32_add", "f32_mul",
     "f32_mad", "fma_peak", "load",
 ]
@@ -91,7 +91,9 @@ def workspace(nbytes: int, device=None, key: str = "reduce") -> torch.Tensor:
 
     Each (device, stream, key) has its own buffer, allocated while that
     stream is current, so calls on one stream reuse it in stream order and
-    calls on different streams never share one."""
+    calls on different streams never share one.  A GEMV-adjoint workspace
+    can be large (row blocks x n x k values); ``clear_workspaces()`` releases
+    every cached buffer."""
     dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
     k = (dev.index, torch.cuda.current_stream(dev).cuda_stream, key)
     buf = _ws_cache.get(k)
@@ -99,6 +101,12 @@ def workspace(nbytes: int, device=None, key: str = "reduce") -> torch.Tensor:
         buf = torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=dev)
         _ws_cache[k] = buf
     return buf
+
+
+def clear_workspaces() -> None:
+    """Drop every cached workspace (the memory returns to PyTorch's caching
+    allocator once the work already enqueued on their streams has run)."""
+    _ws_cache.clear()
 
 
 # ---------------------------------------------------------------------------
