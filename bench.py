@@ -903,6 +903,26 @@ def run_case(args):
         dout = torch.tensor([1.0, 0.0], device=dev)
         fn = {"dot": lambda: ff.dot(x, y), "sum": lambda: ff.sum(x),
               "dot_backward": lambda: ff.dot_backward(dout, x, y)}[args.case]
+    elif args.case == "batch":
+        # 256 dot / AXPY instances, lengths log-uniform over 1e2..1e6 (a small
+        # sample of the 4096-instance workload), one persistent launch
+        from paper_cs_0603115_gb300 import batch
+        lengths, kinds = inputs.batch_lengths(256, inputs.seed_for(3, 0), hi_exp=6.0)
+        offs, o = [], 0
+        for ln in lengths:
+            offs.append(o)
+            o += ln + (ln & 1)
+        gx = torch.Generator(device=dev).manual_seed(inputs.seed_for(3, 11))
+        X = inputs.to_ff(inputs.loguniform_f64(o, gx, dev))
+        Y = inputs.to_ff(inputs.loguniform_f64(o, gx, dev))
+        Z = torch.empty_like(X)
+        D = torch.empty((len(lengths), 2), dtype=torch.float32, device=dev)
+        specs = []
+        for i, (ln, kind) in enumerate(zip(lengths, kinds)):
+            sl = slice(offs[i], offs[i] + ln)
+            specs.append((kind, X[sl], Y[sl], D[i] if kind == batch.DOT else Z[sl], (1.5, 0.0)))
+        plan = batch.BatchPlan(batch.make_instances(specs), tune=(256, 128, 4, 4))
+        fn = plan.run
     elif args.case == "batch_gemv":
         from paper_cs_0603115_gb300 import batch
         g = torch.Generator().manual_seed(inputs.seed_for(3, 9))
