@@ -487,7 +487,8 @@ def extra_rows(torch, ff, inputs, e, dev, peaks):
     a32, b32 = e.a[:, 0].contiguous(), e.b[:, 0].contiguous()
     for name, fn, nb, ops in (("dot_2^28", lambda: ff.dot(e.a, e.b), 16, 2),
                               ("sum_2^28", lambda: ff.sum(e.a), 8, 1),
-                              ("dot2_f32_2^28", lambda: ff.dot2(a32, b32), 8, 2)):
+                              ("dot2_f32_2^28", lambda: ff.dot2(a32, b32), 8, 2),
+                              ("sum2_f32_2^28", lambda: ff.sum2(a32), 4, 1)):
         t = time_fn(torch, fn, 10)
         out[name] = {"ms": round(t * 1e3, 4), "GB/s": round(nb * n / t / 1e9, 1),
                      "frac_hbm": round(nb * n / t / 1e9 / hbm, 4), "ops_s": ops * n / t}
