@@ -948,10 +948,16 @@ def run_case(args):
         g = inputs.gemm(n, n, n, inputs.seed_for(6, 0), device=dev)
         C = torch.empty_like(g.A)
         fn = lambda: ff.gemm(g.A, g.B, out=C)
-    elif args.case in ("gemv", "gemv_t"):
+    elif args.case in ("gemv", "gemv_t", "gemv_dA"):
         m = int(math.isqrt(n))
         gi = inputs.gemv(m, m, args.k, inputs.seed_for(4, 0), device=dev)
-        fn = (lambda: ff.gemv(gi.A, gi.X)) if args.case == "gemv" else (lambda: ff.gemv_t(gi.A, gi.dY))
+        if args.case == "gemv":
+            fn = lambda: ff.gemv(gi.A, gi.X)
+        elif args.case == "gemv_t":
+            fn = lambda: ff.gemv_t(gi.A, gi.dY)
+        else:
+            dA = torch.empty_like(gi.A)
+            fn = lambda: ff.gemv_dA(gi.dY, gi.X, out=dA)
     else:
         e = inputs.elementwise(n, inputs.seed_for(1, 0), device=dev)
         outs = [torch.empty_like(e.a) for _ in OPS]
