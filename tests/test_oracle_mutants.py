@@ -24,6 +24,8 @@ MUTANTS = [
     ("add22: dropped al", "s = (((ah - r) + bh) + bl) + al;", "s = (((ah - r) + bh) + bl);"),
     ("add22: branch test inverted", "if (fabsf(ah) >= fabsf(bh))", "if (fabsf(ah) <= fabsf(bh))"),
     ("add22: second branch uses al twice", "s = (((bh - r) + ah) + al) + bl;", "s = (((bh - r) + ah) + al) + al;"),
+    ("add22: low parts swapped (first branch)", "s = (((ah - r) + bh) + bl) + al;", "s = (((ah - r) + bh) + al) + bl;"),
+    ("add22: low parts swapped (second branch)", "s = (((bh - r) + ah) + al) + bl;", "s = (((bh - r) + ah) + bl) + al;"),
     ("mul22: printed Add12(t1, t2)",
      "    float t3 = ((ah * bl) + (al * bh)) + t2;\n    add12(t1, t3, rh, rl);\n}\n\n/* Mul22 with the paper's own",
      "    float t3 = ((ah * bl) + (al * bh)) + t2;\n    (void)t3;\n    add12(t1, t2, rh, rl);\n}\n\n/* Mul22 with the paper's own"),
@@ -57,7 +59,8 @@ MUTANTS = [
 
 # quick pins first; each mutant stops at the first pin that fails
 PINS = [
-    (pins.test_add22_closed_forms, ()), (pins.test_add22_geometric_series_sum, ()),
+    (pins.test_add22_closed_forms, ()), (pins.test_add22_low_part_order, ()),
+    (pins.test_add22_geometric_series_sum, ()),
     (pins.test_mul22_closed_forms, ()), (pins.test_div22_special_cases, ()),
     (pins.test_sqrt22_special_cases, ()), (pins.test_add22_accurate_special_cases, ()),
     (pins.test_sum_of_ones, ()), (pins.test_dot_with_ones_is_sum_and_n1_is_mul22, ()),

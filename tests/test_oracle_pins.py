@@ -265,6 +265,47 @@ def test_add22_closed_forms(orc):
     assert float(r[0, 0]) + float(r[0, 1]) == 2 + 2.0 ** -27
 
 
+def add22_low_part_order_cases():
+    """Worked examples, derived by hand, in which the order of the two low
+    parts in Add22's s (Section 4.1, Add22 theorem: the low part of the
+    operand with the smaller high part is added first, then the other one)
+    decides the result.
+
+    a = (2^24, 2^-24 + 2^-47), b = (1, 2^-24): |ah| >= |bh|, r = RN(2^24 + 1)
+    = 2^24 (a tie, to even), ah - r = 0, + bh = 1, then
+      paper order   + bl = RN(1 + 2^-24) = 1 (tie, to even),
+                    + al = RN(1 + 2^-24 + 2^-47) = 1 + 2^-23  -> s = 1 + 2^-23
+      swapped order + al = 1 + 2^-23, + bl = RN(1 + 2^-23 + 2^-24)
+                    = 1 + 2^-22 (tie, to even)                -> s = 1 + 2^-22
+    and Add12(r, s) = (RN(2^24 + s), 2^24 + s - RN(2^24 + s)):
+      paper order   (2^24 + 2, -1 + 2^-23); swapped (2^24 + 2, -1 + 2^-22).
+    Exchanging a and b takes the other branch with the same operands in the
+    same roles, so both branches must give the first pair.  Scaling every
+    part by 2^e (no under- or overflow) and negating every part scale and
+    negate the result exactly."""
+    cases = []
+    for e in (-20, 0, 20):
+        for sgn in (1.0, -1.0):
+            k = sgn * 2.0 ** e
+            a = (k * 2.0 ** 24, k * (2.0 ** -24 + 2.0 ** -47))
+            b = (k * 1.0, k * 2.0 ** -24)
+            want = (k * (2.0 ** 24 + 2), k * (-1 + 2.0 ** -23))
+            cases.append((a, b, want))   # first branch  (|ah| >= |bh|)
+            cases.append((b, a, want))   # second branch (|ah| <  |bh|)
+    a = np.array([c[0] for c in cases], np.float32)
+    b = np.array([c[1] for c in cases], np.float32)
+    want = np.array([c[2] for c in cases], np.float32)
+    # every constant above is a binary32 value (no rounding on the way in)
+    for arr, src in ((a, [c[0] for c in cases]), (b, [c[1] for c in cases]), (want, [c[2] for c in cases])):
+        assert np.array_equal(arr.astype(np.float64), np.array(src, np.float64))
+    return a, b, want
+
+
+def test_add22_low_part_order(orc):
+    a, b, want = add22_low_part_order_cases()
+    np.testing.assert_array_equal(bits(orc.add22(a, b)), bits(want))
+
+
 def test_add22_geometric_series_sum(orc):
     # sum_{i=0}^{40} 2^-i = 2 - 2^-40 = (2, -2^-40) exactly
     x = np.stack([2.0 ** -np.arange(41), np.zeros(41)], 1).astype(np.float32)

@@ -131,6 +131,17 @@ def test_special_values():
     same_bits(ff.mul12(gpu(torch.from_numpy(ab))).cpu().numpy(), oracle.mul12(ab))
 
 
+def test_add22_low_part_order_worked_examples():
+    """The hand-derived cases in which the order of Add22's two low parts
+    (Section 4.1, Add22 theorem) decides the bits: the GPU's select form
+    gives the paper's order in both branches, like the oracle."""
+    from test_oracle_pins import add22_low_part_order_cases
+    a, b, want = add22_low_part_order_cases()
+    got = ff.add(gpu(torch.from_numpy(a)), gpu(torch.from_numpy(b))).cpu().numpy()
+    same_bits(got, want)
+    same_bits(got, oracle.add22(a, b))
+
+
 def test_subnormal_results_not_flushed():
     ab = np.array([[2.0 ** -140, 2.0 ** -149], [2.0 ** -70, 2.0 ** -70], [1e-20, 1e-20]], np.float32)
     got = ff.add12(gpu(torch.from_numpy(ab))).cpu().numpy()
