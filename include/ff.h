@@ -120,8 +120,14 @@ FF_API ff_status ff_axpy(ff2 alpha, const ff2* x, const ff2* y, ff2* z, size_t n
 /* Compensated reductions (future work of Section 7)                       */
 /* ------------------------------------------------------------------------ */
 
-/* Workspace bytes for ff_sum / ff_dot / ff_f64_dot on the current device
- * (independent of n above a small size; always > 0). */
+/* Workspace bytes for ff_sum / ff_dot / ff_sum2 / ff_dot2 / ff_f64_dot on
+ * the current device (independent of n above a small size; always > 0).
+ * A reduction workspace starts with a 4-byte arrival ticket that must be
+ * zero before the first call that uses the workspace (clear the whole
+ * buffer once when it is allocated, e.g. with cudaMemsetAsync); every call
+ * leaves it zero again when its kernel ends, so later calls need no
+ * clearing.  Storing anything else in the workspace between calls (or a
+ * device fault during a call) requires clearing it again. */
 FF_API size_t ff_reduce_workspace_bytes(size_t n);
 
 /* *out_dev = the float-float sum of x[0..n) by Add22.  Order: thread t of a
@@ -130,8 +136,9 @@ FF_API size_t ff_reduce_workspace_bytes(size_t n);
  * (0, 0); each warp then combines its 32 lanes by a shuffle-down tree, each
  * block its warps likewise, and the last block to finish combines the
  * per-block partials in block order.  ws: caller-owned device workspace of
- * at least ff_reduce_workspace_bytes(n) bytes, 16-byte aligned; it is
- * written by the call and must not be used concurrently by another call.
+ * at least ff_reduce_workspace_bytes(n) bytes, 16-byte aligned, its ticket
+ * zero (see ff_reduce_workspace_bytes); it is written by the call and must
+ * not be used concurrently by another call.  One launch, no memset.
  * Error bound for the stored result r: |r - sum x_i| <= n 2^-46 sum |x_i|. */
 FF_API ff_status ff_sum(const ff2* x, size_t n, ff2* out_dev, void* ws, size_t ws_bytes, cudaStream_t s);
 
@@ -244,8 +251,11 @@ FF_API ff_status ff_gemv_t_launch_shape(const ff2* A, int64_t m, int64_t n, int6
  * Mul22(dY[r, c], X[j, c]), accumulated with Add22 in order c = 0 .. k-1
  * (bit-reproducible).  dY: m x k column-major (lddy >= m); X: n x k
  * column-major (ldx >= n); dA: m x n row-major (ldda >= n), overwritten;
- * it must not overlap dY or X.  1 <= k <= 64.  From k = 5 on the call runs
- * ff_gemm (transa = 1 on dY), which forms the same terms in the same order. */
+ * it must not overlap dY or X.  1 <= k <= 64.  Every element starts from
+ * (0, 0) as the sum's definition says; its first Add22 (with the zero) is
+ * formed in two additions when the term is a finite normalised pair (the
+ * same bits), the full Add22 otherwise.  From k = 9 on the call runs ff_gemm
+ * (transa = 1 on dY), which forms the same terms in the same order. */
 FF_API ff_status ff_gemv_dA(const ff2* dY, int64_t m, int64_t lddy, const ff2* X, int64_t n, int64_t ldx,
                             int64_t k, ff2* dA, int64_t ldda, cudaStream_t s);
 

@@ -300,49 +300,142 @@ gemv_dA_scalar_kernel(const float2* __restrict__ dY, int64_t m, int64_t lddy, co
     }
 }
 
-// dA for k <= 4 with 16-byte access: the thread's k column-pair values of X
-// stay in registers, and each row pair's 2k values of dY are loaded before
-// any is used; same per-element order (c = 0 .. k-1 from (0, 0)).
+// Rows per shared-memory chunk of dY in the weight-gradient kernel (even).
+constexpr int kTChunk = 128;
+
+// Add22((+0, +0), t) bit for bit, with two additions instead of the full
+// sequence when t is a finite pair whose sum rounds to its high part (every
+// Mul22 result is one: it ends with Add12).  For such t the Add22 theorem's
+// steps reduce to r = th (+) 0, s = tl (+) 0 and Add12(r, s) = (r, s):
+// th - r = +0 (the tie branch when th = +-0, which forces tl = +-0), the zero
+// operand's low part adds nothing, and Add12 of a pair whose sum rounds to its
+// first part returns the pair.  "(+) 0" does what the full sequence does to a
+// negative zero (it becomes +0).  Any other t (infinite, NaN, not normalised)
+// takes the full sequence.  The test is voted over the warp so that the
+// branch never diverges; every lane of the warp must be present.
+__device__ __forceinline__ bool from_zero_fast(float2 t)
+{
+    return fabsf(t.x) <= 3.40282347e38f && __fadd_rn(t.x, t.y) == t.x;
+}
+
+__device__ __forceinline__ float2 add22_from_zero(float2 t, bool warp_fast)
+{
+    if (warp_fast) return make_float2(__fadd_rn(t.x, 0.0f), __fadd_rn(t.y, 0.0f));
+    return ffk::add22(make_float2(0.0f, 0.0f), t);
+}
+
+// dA for k <= 8 with 16-byte access along the rows of dA: one thread per
+// pair of adjacent columns, the thread's k column-pair values of X in
+// registers.  Block row y takes the rows [y rpb, (y + 1) rpb) (rpb even) in
+// pairs, so a thread forms 4 elements per step; the block stages the dY
+// values of kTChunk rows at a time in shared memory, where one 16-byte read
+// gives both rows of a pair for one right-hand side.  Every element is
+// Add22((0, 0), term_0), then Add22 of terms 1 .. k-1, in order (the first
+// step through add22_from_zero, bit-identical).  Lanes past the last column
+// pair work on the last pair and do not store, so that every lane of a warp
+// takes part in the vote and every thread reaches the block barriers.
 template <int KT>
 __global__ void __launch_bounds__(kGBlock)
 gemv_dA_small_kernel(const float2* __restrict__ dY, int64_t m, int64_t lddy, const float2* __restrict__ X, int64_t n,
-                     int64_t ldx, float2* __restrict__ dA, int64_t ldda)
+                     int64_t ldx, float2* __restrict__ dA, int64_t ldda, int64_t rpb)
 {
-    const int64_t gy = gridDim.y;
-    const int64_t jp = static_cast<int64_t>(blockIdx.x) * kGBlock + threadIdx.x;
-    if (2 * jp >= n) return;
-    float4 x[KT];
+    __shared__ float4 sdy[KT][kTChunk / 2];
+    const int64_t npairs = n >> 1;
+    const int64_t jp_raw = static_cast<int64_t>(blockIdx.x) * kGBlock + threadIdx.x;
+    if (static_cast<int64_t>(blockIdx.x) * kGBlock >= npairs) return;  // whole block past the end
+    const bool store = jp_raw < npairs;
+    const int64_t jp = store ? jp_raw : npairs - 1;
+    float2 xl[KT], xh[KT];
 #pragma unroll
-    for (int c = 0; c < KT; ++c) x[c] = __ldg(reinterpret_cast<const float4*>(X + c * ldx) + jp);
-    int64_t r = blockIdx.y;
-    for (; r + gy < m; r += 2 * gy) {
-        const int64_t r1 = r + gy;
-        float2 d0[KT], d1[KT];
-#pragma unroll
-        for (int c = 0; c < KT; ++c) {
-            d0[c] = __ldg(dY + c * lddy + r);
-            d1[c] = __ldg(dY + c * lddy + r1);
-        }
-        float2 a00 = make_float2(0.0f, 0.0f), a01 = a00, a10 = a00, a11 = a00;
-#pragma unroll
-        for (int c = 0; c < KT; ++c) {
-            a00 = ffk::add22(a00, ffk::mul22(d0[c], make_float2(x[c].x, x[c].y)));
-            a01 = ffk::add22(a01, ffk::mul22(d0[c], make_float2(x[c].z, x[c].w)));
-            a10 = ffk::add22(a10, ffk::mul22(d1[c], make_float2(x[c].x, x[c].y)));
-            a11 = ffk::add22(a11, ffk::mul22(d1[c], make_float2(x[c].z, x[c].w)));
-        }
-        __stcs(reinterpret_cast<float4*>(dA + r * ldda) + jp, make_float4(a00.x, a00.y, a01.x, a01.y));
-        __stcs(reinterpret_cast<float4*>(dA + r1 * ldda) + jp, make_float4(a10.x, a10.y, a11.x, a11.y));
+    for (int c = 0; c < KT; ++c) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(X + c * ldx) + jp);
+        xl[c] = make_float2(v.x, v.y);
+        xh[c] = make_float2(v.z, v.w);
     }
-    if (r < m) {
-        float2 a0 = make_float2(0.0f, 0.0f), a1 = a0;
-#pragma unroll
-        for (int c = 0; c < KT; ++c) {
-            const float2 d = __ldg(dY + c * lddy + r);
-            a0 = ffk::add22(a0, ffk::mul22(d, make_float2(x[c].x, x[c].y)));
-            a1 = ffk::add22(a1, ffk::mul22(d, make_float2(x[c].z, x[c].w)));
+    const int64_t r0 = static_cast<int64_t>(blockIdx.y) * rpb;
+    const int64_t r1 = r0 + rpb < m ? r0 + rpb : m;
+    const int64_t rp = r0 + ((r1 > r0 ? r1 - r0 : 0) & ~static_cast<int64_t>(1));   // end of the row pairs
+    for (int64_t cb = r0; cb < rp; cb += kTChunk) {
+        const int rows = static_cast<int>(rp - cb < kTChunk ? rp - cb : kTChunk);
+        __syncthreads();   // the previous chunk's reads are done
+        for (int i = threadIdx.x; i < KT * kTChunk; i += kGBlock) {
+            const int c = i / kTChunk, q = i - c * kTChunk;
+            if (q < rows) reinterpret_cast<float2*>(sdy[c])[q] = __ldg(dY + c * lddy + cb + q);
         }
-        __stcs(reinterpret_cast<float4*>(dA + r * ldda) + jp, make_float4(a0.x, a0.y, a1.x, a1.y));
+        __syncthreads();
+        float4* row = reinterpret_cast<float4*>(dA + cb * ldda) + jp;
+        const int64_t ldda4 = ldda >> 1;
+        for (int lp = 0; lp < rows / 2; ++lp, row += 2 * ldda4) {
+            float4 d01 = sdy[0][lp];
+            const float2 t00 = ffk::mul22(make_float2(d01.x, d01.y), xl[0]);
+            const float2 t01 = ffk::mul22(make_float2(d01.x, d01.y), xh[0]);
+            const float2 t10 = ffk::mul22(make_float2(d01.z, d01.w), xl[0]);
+            const float2 t11 = ffk::mul22(make_float2(d01.z, d01.w), xh[0]);
+            const bool fast = __all_sync(0xffffffffu, from_zero_fast(t00) && from_zero_fast(t01) &&
+                                                          from_zero_fast(t10) && from_zero_fast(t11));
+            float2 a00 = add22_from_zero(t00, fast), a01 = add22_from_zero(t01, fast);
+            float2 a10 = add22_from_zero(t10, fast), a11 = add22_from_zero(t11, fast);
+#pragma unroll
+            for (int c = 1; c < KT; ++c) {
+                d01 = sdy[c][lp];
+                const float2 d0 = make_float2(d01.x, d01.y), d1 = make_float2(d01.z, d01.w);
+                a00 = ffk::add22(a00, ffk::mul22(d0, xl[c]));
+                a01 = ffk::add22(a01, ffk::mul22(d0, xh[c]));
+                a10 = ffk::add22(a10, ffk::mul22(d1, xl[c]));
+                a11 = ffk::add22(a11, ffk::mul22(d1, xh[c]));
+            }
+            if (store) {
+                __stcs(row, make_float4(a00.x, a00.y, a01.x, a01.y));
+                __stcs(row + ldda4, make_float4(a10.x, a10.y, a11.x, a11.y));
+            }
+        }
+    }
+    if (rp < r1) {  // the last row of an odd m
+        const int64_t r = rp;
+        const float2 d = __ldg(dY + r);
+        const float2 t0 = ffk::mul22(d, xl[0]), t1 = ffk::mul22(d, xh[0]);
+        const bool fast = __all_sync(0xffffffffu, from_zero_fast(t0) && from_zero_fast(t1));
+        float2 a0 = add22_from_zero(t0, fast), a1 = add22_from_zero(t1, fast);
+#pragma unroll
+        for (int c = 1; c < KT; ++c) {
+            const float2 dc = __ldg(dY + c * lddy + r);
+            a0 = ffk::add22(a0, ffk::mul22(dc, xl[c]));
+            a1 = ffk::add22(a1, ffk::mul22(dc, xh[c]));
+        }
+        if (store) __stcs(reinterpret_cast<float4*>(dA + r * ldda) + jp, make_float4(a0.x, a0.y, a1.x, a1.y));
+    }
+}
+
+// Widest k that ff_gemv_dA runs on gemv_dA_small_kernel (the GEMM kernel
+// takes larger k).
+constexpr int kDAMaxSmallK = 8;
+
+const void* dA_small_ptr(int k)
+{
+    switch (k) {
+    case 1: return reinterpret_cast<const void*>(&gemv_dA_small_kernel<1>);
+    case 2: return reinterpret_cast<const void*>(&gemv_dA_small_kernel<2>);
+    case 3: return reinterpret_cast<const void*>(&gemv_dA_small_kernel<3>);
+    case 4: return reinterpret_cast<const void*>(&gemv_dA_small_kernel<4>);
+    case 5: return reinterpret_cast<const void*>(&gemv_dA_small_kernel<5>);
+    case 6: return reinterpret_cast<const void*>(&gemv_dA_small_kernel<6>);
+    case 7: return reinterpret_cast<const void*>(&gemv_dA_small_kernel<7>);
+    default: return reinterpret_cast<const void*>(&gemv_dA_small_kernel<8>);
+    }
+}
+
+void launch_dA_small(int k, dim3 grid, cudaStream_t s, const float2* dY, int64_t m, int64_t lddy, const float2* X,
+                     int64_t n, int64_t ldx, float2* dA, int64_t ldda, int64_t rpb)
+{
+    switch (k) {
+    case 1: gemv_dA_small_kernel<1><<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, dA, ldda, rpb); break;
+    case 2: gemv_dA_small_kernel<2><<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, dA, ldda, rpb); break;
+    case 3: gemv_dA_small_kernel<3><<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, dA, ldda, rpb); break;
+    case 4: gemv_dA_small_kernel<4><<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, dA, ldda, rpb); break;
+    case 5: gemv_dA_small_kernel<5><<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, dA, ldda, rpb); break;
+    case 6: gemv_dA_small_kernel<6><<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, dA, ldda, rpb); break;
+    case 7: gemv_dA_small_kernel<7><<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, dA, ldda, rpb); break;
+    default: gemv_dA_small_kernel<8><<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, dA, ldda, rpb); break;
     }
 }
 
@@ -512,11 +605,11 @@ ff_status ff_gemv_dA(const ff2* dY_, int64_t m, int64_t lddy, const ff2* X_, int
     if (!ffh::ok_ptr(dY_, static_cast<size_t>(m)) || !ffh::ok_ptr(X_, static_cast<size_t>(n)) || !ffh::ok_ptr(dA_, an))
         return FF_ERR_INVALID_ARG;
     if (m == 0 || n == 0) return FF_OK;
-    // from five right-hand sides on, dA is a matrix product op(dY) X with dY
-    // read transposed in place: the GEMM kernel computes every element with
-    // the same Mul22(dY[r, c], X[j, c]) terms in the same order (bit-identical)
-    // at its higher arithmetic rate
-    if (k > 4) return ff_gemm(1, 0, m, n, k, dY_, lddy, X_, ldx, dA_, ldda, s);
+    // beyond kDAMaxSmallK right-hand sides, dA is a matrix product op(dY) X
+    // with dY read transposed in place: the GEMM kernel computes every
+    // element with the same Mul22(dY[r, c], X[j, c]) terms in the same order
+    // (bit-identical) at its higher arithmetic rate
+    if (k > kDAMaxSmallK) return ff_gemm(1, 0, m, n, k, dY_, lddy, X_, ldx, dA_, ldda, s);
     auto* dY = reinterpret_cast<const float2*>(dY_);
     auto* X = reinterpret_cast<const float2*>(X_);
     auto* dA = reinterpret_cast<float2*>(dA_);
@@ -525,26 +618,26 @@ ff_status ff_gemv_dA(const ff2* dY_, int64_t m, int64_t lddy, const ff2* X_, int
     const ff_status st = ffh::device_info(&di);
     if (st != FF_OK) return st;
     // one wave of resident blocks (rounded down so that every block is
-    // resident at once: all walk the same number of rows); every block walks
-    // rows blockIdx.y, blockIdx.y + gridDim.y, ...
+    // resident at once)
     const int64_t col_blocks = ((vec ? n / 2 : n) + kGBlock - 1) / kGBlock;
-    const int occ = ffh::occupancy(vec ? reinterpret_cast<const void*>(&gemv_dA_small_kernel<4>)
-                                       : reinterpret_cast<const void*>(&gemv_dA_scalar_kernel), kGBlock);
+    const void* kern = vec ? dA_small_ptr(static_cast<int>(k)) : reinterpret_cast<const void*>(&gemv_dA_scalar_kernel);
+    const int occ = ffh::occupancy(kern, kGBlock);
     int64_t gy64 = static_cast<int64_t>(di.sm_count) * (occ > 0 ? occ : 1) / col_blocks;
-    if (gy64 > m) gy64 = m;
-    if (gy64 > 65535) gy64 = 65535;
-    if (gy64 < 1) gy64 = 1;
-    const unsigned gy = static_cast<unsigned>(gy64);
     if (vec) {
-        dim3 grid(static_cast<unsigned>((n / 2 + kGBlock - 1) / kGBlock), gy);
-        switch (k) {
-        case 1: gemv_dA_small_kernel<1><<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, dA, ldda); break;
-        case 2: gemv_dA_small_kernel<2><<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, dA, ldda); break;
-        case 3: gemv_dA_small_kernel<3><<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, dA, ldda); break;
-        default: gemv_dA_small_kernel<4><<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, dA, ldda); break;
-        }
+        // block rows of an even number of rows, every block row non-empty
+        if (gy64 > (m + 1) / 2) gy64 = (m + 1) / 2;
+        if (gy64 > 65535) gy64 = 65535;
+        if (gy64 < 1) gy64 = 1;
+        int64_t rpb = (m + gy64 - 1) / gy64;
+        rpb += rpb & 1;
+        gy64 = (m + rpb - 1) / rpb;
+        dim3 grid(static_cast<unsigned>((n / 2 + kGBlock - 1) / kGBlock), static_cast<unsigned>(gy64));
+        launch_dA_small(static_cast<int>(k), grid, s, dY, m, lddy, X, n, ldx, dA, ldda, rpb);
     } else {
-        dim3 grid(static_cast<unsigned>((n + kGBlock - 1) / kGBlock), gy);
+        if (gy64 > m) gy64 = m;
+        if (gy64 > 65535) gy64 = 65535;
+        if (gy64 < 1) gy64 = 1;
+        dim3 grid(static_cast<unsigned>((n + kGBlock - 1) / kGBlock), static_cast<unsigned>(gy64));
         gemv_dA_scalar_kernel<<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, k, dA, ldda);
     }
     return ffh::check_launch();

@@ -455,7 +455,8 @@ def test_gemv_bitexact_vs_order_replay(m, n, k):
     same_bits(Y, replay.gemv_warp_replay(gi.A.numpy(), gi.X.numpy(), vec=(n % 2 == 0)))
 
 
-@pytest.mark.parametrize("m,n,k", [(4096, 256, 3), (3000, 130, 2), (70, 513, 5), (31, 8, 1)])
+@pytest.mark.parametrize("m,n,k", [(4096, 256, 3), (3000, 130, 2), (70, 513, 5), (31, 8, 1), (5000, 770, 7),
+                                   (4099, 66, 4), (1027, 1030, 6), (2500, 518, 9), (8191, 64, 1)])
 def test_gemv_t_bitexact_vs_order_replay(m, n, k):
     """ff_gemv_t bit for bit against the replay of its row-block order (the
     row-block count read from ff_gemv_t_launch_shape)."""
@@ -485,11 +486,33 @@ def test_gemv_result_does_not_depend_on_k(n):
 
 
 @pytest.mark.parametrize("m,n,k", [(33, 64, 1), (17, 129, 5), (64, 256, 64), (17, 129, 3), (301, 1000, 4),
-                                   (300, 998, 2)])
+                                   (300, 998, 2), (257, 66, 7), (256, 514, 8), (1000, 2050, 5), (999, 130, 6),
+                                   (40, 20, 9)])
 def test_gemv_dA_bitexact(m, n, k):
     gi = inputs.gemv(m, n, k, inputs.seed_for(4, 50 + k))
     dA = ff.gemv_dA(gpu(gi.dY), gpu(gi.X)).cpu().numpy()
     same_bits(dA, oracle.gemv_dA(gi.dY.numpy(), gi.X.numpy()))
+
+
+@pytest.mark.parametrize("m,n,k", [(130, 66, 1), (129, 128, 2), (64, 70, 3), (66, 64, 8)])
+def test_gemv_dA_special_values_bitexact(m, n, k):
+    """dA's first term takes a shortcut for finite normalised products and
+    the full Add22 from (0, 0) otherwise: signed zeros, subnormals,
+    overflowing products, infinities and NaN planted in dY and X give the
+    oracle's bits (NaN == NaN), for warps that see them and warps that do
+    not."""
+    gi = inputs.gemv(m, n, k, inputs.seed_for(4, 70 + k))
+    dY, X = gi.dY.numpy().copy(), gi.X.numpy().copy()
+    rng = np.random.default_rng(17 + k)
+    specials = np.array([(0.0, 0.0), (-0.0, 0.0), (-0.0, -0.0), (2.0 ** -149, 0.0), (-(2.0 ** -140), 2.0 ** -149),
+                         (3e38, 1e30), (-3e38, 0.0), (np.inf, 0.0), (-np.inf, 0.0), (np.nan, 0.0), (1.0, np.nan),
+                         (2.0 ** 100, 2.0 ** 76), (1.0, 1.0)], np.float32)
+    for arr, rows in ((dY, m), (X, n)):
+        for _ in range(max(4, rows // 8)):
+            c, i = rng.integers(0, k), rng.integers(0, rows)
+            arr[c, i] = specials[rng.integers(0, len(specials))]
+    dA = ff.gemv_dA(gpu(torch.from_numpy(dY)), gpu(torch.from_numpy(X))).cpu().numpy()
+    same_bits(dA, oracle.gemv_dA(dY, X))
 
 
 def test_gemv_autograd_weight_gradient():
