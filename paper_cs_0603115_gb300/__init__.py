@@ -91,14 +91,16 @@ def workspace(nbytes: int, device=None, key: str = "reduce") -> torch.Tensor:
 
     Each (device, stream, key) has its own buffer, allocated while that
     stream is current, so calls on one stream reuse it in stream order and
-    calls on different streams never share one.  A GEMV-adjoint workspace
-    can be large (row blocks x n x k values); ``clear_workspaces()`` releases
-    every cached buffer."""
+    calls on different streams never share one.  Buffers start zeroed (a
+    reduction workspace's arrival ticket must be zero before its first use;
+    each reduction leaves it zero).  A GEMV-adjoint workspace can be large
+    (row blocks x n x k values); ``clear_workspaces()`` releases every cached
+    buffer."""
     dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
     k = (dev.index, torch.cuda.current_stream(dev).cuda_stream, key)
     buf = _ws_cache.get(k)
     if buf is None or buf.numel() < nbytes:
-        buf = torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=dev)
+        buf = torch.zeros(max(int(nbytes), 256), dtype=torch.uint8, device=dev)
         _ws_cache[k] = buf
     return buf
 

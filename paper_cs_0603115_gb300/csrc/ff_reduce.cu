@@ -16,7 +16,9 @@
 //      values with the same tree (off = 4, 2, 1);
 //   4. every block stores its value in the workspace; the last block to
 //      arrive (atomic ticket) accumulates the block values b, b + 256, ... per
-//      thread, from zero, and reduces them with steps 2-3.
+//      thread, from zero, and reduces them with steps 2-3, then sets the
+//      ticket back to zero (the caller zeroes a workspace once, before its
+//      first use, so a call is a single launch).
 // No block ever waits for another.
 #include <mutex>
 
@@ -312,10 +314,8 @@ ff_status run_reduce(const typename P::T* x, const typename P::T* y, size_t n, t
     unsigned* ticket = static_cast<unsigned*>(ws);
     auto* partials = reinterpret_cast<typename P::Acc*>(static_cast<char*>(ws) + kPartialsOffset);
     const Shape sh = shape_for<P>(x, y, n, di);
-    if (sh.grid > 1) {
-        st = ffh::cuda_status(cudaMemsetAsync(ticket, 0, sizeof(unsigned), s));
-        if (st != FF_OK) return st;
-    }
+    // No clearing launch: the ticket is zero on entry (the workspace contract)
+    // and the last block resets it to zero before the kernel ends.
     if (sh.vec)
         reduce_kernel<P, kU><<<sh.grid, kRBlock, 0, s>>>(x, y, n, sh.head, out, partials, ticket);
     else
