@@ -9,9 +9,13 @@ collective sum (e.g. NCCL's SUM) cannot be used: it would add the high and
 the low parts separately.
 
 GEMV needs no exchange when A is sharded by rows (each rank owns its rows of
-Y); its adjoint dX = A^T dY does: every rank computes the (n, k) partial of
-its rows, the partials are all-gathered and added in rank order with Add22
-(ff_add, one launch per rank after the first).
+Y); its adjoint dX = A^T dY does: every rank computes the (k, n) partial of
+its rows.  The columns are cut into one contiguous block per rank; rank b
+receives every rank's partial of block b (point-to-point sends), adds them
+in rank order with Add22 (ff_add) and the combined blocks are all-gathered.
+Each column sees the same rank-ordered Add22 sequence as if every rank
+combined all partials, for 1/world of the exchanged bytes and of the
+additions.
 
 The compute functions are arguments (defaulting to the library's kernels)
 so that the exchange logic can be exercised on CPU-only ranks with stand-ins.
@@ -66,20 +70,56 @@ def sharded_sum(x_local: torch.Tensor, group=None, sum_fn=None):
     return combine_partials(parts, sum_fn)
 
 
+def _exchange(send: list, recv: list, group=None) -> None:
+    """recv[r] = rank r's send[this rank] for every other rank r (point to
+    point; empty blocks are neither sent nor received)."""
+    import torch.distributed as dist
+    rank = dist.get_rank(group)
+    ops = []
+    for r in range(len(send)):
+        if r == rank:
+            continue
+        peer = dist.get_global_rank(group, r) if group is not None else r
+        if send[r].numel():
+            ops.append(dist.P2POp(dist.isend, send[r], peer, group))
+        if recv[r].numel():
+            ops.append(dist.P2POp(dist.irecv, recv[r], peer, group))
+    if ops:
+        for req in dist.batch_isend_irecv(ops):
+            req.wait()
+
+
 def sharded_gemv_t(A_local: torch.Tensor, dY_local: torch.Tensor, group=None, gemv_t_fn=None, add_fn=None):
     """dX = A^T dY for A sharded by rows: A_local (m_r, n, 2) and dY_local
     (k, m_r, 2) are this rank's rows.  Returns the (k, n, 2) dX, equal on every
-    rank: the per-rank partials are added in rank order with Add22."""
+    rank: for every column the per-rank partials are added in rank order with
+    Add22.  Exchange: reduce-scatter by column block (each rank combines the
+    block shard_range(n, rank, world) of every rank's partial), then an
+    all-gather of the combined blocks."""
+    import torch.distributed as dist
     if gemv_t_fn is None:
         from . import gemv_t as gemv_t_fn
     if add_fn is None:
         from . import add as add_fn
     local = gemv_t_fn(A_local, dY_local)
-    parts = _all_gather_rows(local, group)
-    acc = parts[0].contiguous()
-    for r in range(1, parts.shape[0]):
-        acc = add_fn(acc, parts[r].contiguous())
-    return acc
+    world, rank = dist.get_world_size(group), dist.get_rank(group)
+    k, n = local.shape[0], local.shape[1]
+    if world == 1 or n == 0:
+        return local
+    spans = [shard_range(n, b, world) for b in range(world)]
+    lo, hi = spans[rank]
+    send = [local[:, a:b].contiguous() for a, b in spans]
+    recv = [send[r] if r == rank else torch.empty((k, hi - lo, 2), dtype=local.dtype, device=local.device)
+            for r in range(world)]
+    _exchange(send, recv, group)
+    acc = recv[0]
+    for r in range(1, world):
+        acc = add_fn(acc.contiguous(), recv[r].contiguous())
+    width = max(b - a for a, b in spans)
+    mine = torch.zeros((k, width, 2), dtype=local.dtype, device=local.device)
+    mine[:, :hi - lo] = acc
+    blocks = _all_gather_rows(mine, group)
+    return torch.cat([blocks[b, :, :spans[b][1] - spans[b][0]] for b in range(world)], dim=1).contiguous()
 
 
 def partition_instances(nbytes, world: int) -> list[list[int]]:
