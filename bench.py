@@ -178,6 +178,25 @@ def time_fn(torch, fn, reps: int, warm: int = 2) -> float:
     return ev0.elapsed_time(ev1) / 1e3 / reps
 
 
+def time_median(torch, fn, reps: int, warm: int = 2) -> float:
+    """Median seconds per call over `reps` calls, each between its own pair
+    of CUDA events on the current stream (for calls of a millisecond or more,
+    where one call's events cost nothing next to it)."""
+    for _ in range(warm):
+        fn()
+    s = torch.cuda.current_stream()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    torch.cuda.synchronize()
+    for e0, e1 in evs:
+        e0.record(s)
+        fn()
+        e1.record(s)
+    torch.cuda.synchronize()
+    ts = sorted(e0.elapsed_time(e1) / 1e3 for e0, e1 in evs)
+    mid = len(ts) // 2
+    return ts[mid] if len(ts) % 2 else 0.5 * (ts[mid - 1] + ts[mid])
+
+
 def host_cores() -> int:
     try:
         return len(os.sched_getaffinity(0))
@@ -549,9 +568,9 @@ def extra_rows(torch, ff, inputs, e, dev, peaks):
     dA = torch.empty_like(A)   # the weight gradient dY X^T: one write of every A value
     for k in ks:
         X = Xall[:k].contiguous()
-        tf = time_fn(torch, lambda: ff.gemv(A, X), 2, warm=1)
-        tb = time_fn(torch, lambda: ff.gemv_t(A, X), 2, warm=1)
-        tw = time_fn(torch, lambda: ff.gemv_dA(X, X, out=dA), 2, warm=1)
+        tf = time_median(torch, lambda: ff.gemv(A, X), 11, warm=2)
+        tb = time_median(torch, lambda: ff.gemv_t(A, X), 11, warm=2)
+        tw = time_median(torch, lambda: ff.gemv_dA(X, X, out=dA), 11, warm=2)
         tot_f += tf
         tot_b += tb
         t_bound = max(8 * M * N / (hbm * 1e9), 28 * M * N * k / fp32)   # roofline time of one call
@@ -561,7 +580,9 @@ def extra_rows(torch, ff, inputs, e, dev, peaks):
                        "fwd_frac_roofline": round(t_bound / tf, 4), "adj_frac_roofline": round(t_bound / tb, 4),
                        "dA_frac_roofline": round(t_bound / tw, 4)}
     del dA
-    out["gemv_32768^2"] = {"per_k": gem, "sweep_fwd_ms": round(tot_f * 1e3, 2), "sweep_adj_ms": round(tot_b * 1e3, 2),
+    out["gemv_32768^2"] = {"per_k": gem, "timing": "median of 11 calls after 2 warm-ups, each call between "
+                                                   "its own CUDA events",
+                           "sweep_fwd_ms": round(tot_f * 1e3, 2), "sweep_adj_ms": round(tot_b * 1e3, 2),
                            "k1_fwd_GB/s": round(8 * M * N / (gem["1"]["fwd_ms"] / 1e3) / 1e9, 1)}
     A64 = inputs.ff_to_f64(A)
     del A

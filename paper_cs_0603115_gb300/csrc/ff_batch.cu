@@ -12,14 +12,11 @@
 // round robin (block b takes tiles b, b + G, b + 2G, ...).
 //   AXPY tile: z_i = Add22(Mul22(alpha, x_i), y_i) for the tile's values.
 //   dot-gradient tile: dx_i = Mul22(dout, y_i), dy_i = Mul22(dout, x_i).
-//   GEMV rows tile (rows of length <= 65536): warp w of the block reduces
-//   rows start + w R .. start + w R + R - 1 in turn (R rows per warp, chosen
-//   at plan time so that a tile holds about 16K values).  Lane l accumulates the row's two-value chunks with
-//   Add22(acc, Mul22(A_rj, x_j)) into two accumulators (chunks l + 128i and
-//   l + 64 + 128i into the first, l + 32 + 128i and l + 96 + 128i into the
-//   second, leftover chunks into the first), adds them, the warp combines
-//   its lanes with the shuffle-down Add22 tree and lane 0 writes out[r].  Longer GEMV
-//   rows become dot records (row r of the matrix with the vector).
+//   GEMV rows tile (rows of length <= 65536): eight lanes reduce one row,
+//   so a warp works on four rows at a time, R groups of four rows per warp
+//   per tile (R chosen at plan time so that a tile holds about 16K values);
+//   the exact lane and chunk order is given at gemv_rows_tile_body.  Longer
+//   GEMV rows become dot records (row r of the matrix with the vector).
 //   dot tile:  each thread accumulates its values left to right with
 //              Add22(acc, Mul22(x_i, y_i)); the block combines threads with
 //              the shuffle-down Add22 tree of ff_dot and stores the tile's
