@@ -503,25 +503,31 @@ def extra_rows(torch, ff, inputs, e, dev, peaks):
     # the reductions at the elementwise size (2^28 values of the same arrays):
     # the fixed cost of a launch (ticket memset, ramp, last-block combine) is
     # a quarter of its share at 2^26
+    # reductions: "ms" is the device time per call (20 calls replayed from one
+    # CUDA graph, so host launch gaps between calls do not count); "loop_ms"
+    # the same calls issued one by one from Python
+    red_out = torch.empty(2, dtype=torch.float32, device=dev)
+
+    def red_row(fn, nbytes, nops, key):
+        t = graph_time(torch, fn, 20)
+        tl = time_fn(torch, fn, 10)
+        return {"ms": round(t * 1e3, 4), "loop_ms": round(tl * 1e3, 4), "GB/s": round(nbytes / t / 1e9, 1),
+                "frac_hbm": round(nbytes / t / 1e9 / hbm, 4), "frac_hbm_loop": round(nbytes / tl / 1e9 / hbm, 4),
+                key: nops / t}
+
     a32, b32 = e.a[:, 0].contiguous(), e.b[:, 0].contiguous()
-    for name, fn, nb, ops in (("dot_2^28", lambda: ff.dot(e.a, e.b), 16, 2),
-                              ("sum_2^28", lambda: ff.sum(e.a), 8, 1),
-                              ("dot2_f32_2^28", lambda: ff.dot2(a32, b32), 8, 2),
-                              ("sum2_f32_2^28", lambda: ff.sum2(a32), 4, 1)):
-        t = time_fn(torch, fn, 10)
-        out[name] = {"ms": round(t * 1e3, 4), "GB/s": round(nb * n / t / 1e9, 1),
-                     "frac_hbm": round(nb * n / t / 1e9 / hbm, 4), "ops_s": ops * n / t}
+    for name, fn, nb, ops in (("dot_2^28", lambda: ff.dot(e.a, e.b, out=red_out), 16, 2),
+                              ("sum_2^28", lambda: ff.sum(e.a, out=red_out), 8, 1),
+                              ("dot2_f32_2^28", lambda: ff.dot2(a32, b32, out=red_out), 8, 2),
+                              ("sum2_f32_2^28", lambda: ff.sum2(a32, out=red_out), 4, 1)):
+        out[name] = red_row(fn, nb * n, ops * n, "ops_s")
     del a32, b32
     torch.cuda.empty_cache()
     # compensated Sum2 / Dot2 of binary32 vectors, n = 2^26 (4 / 8 B per value)
     nd2 = 1 << 26
     g2 = inputs.ill_dot_f32(nd2, 1e12, inputs.seed_for(5, 12), device=dev)
-    t = time_fn(torch, lambda: ff.dot2(g2.x, g2.y), 10)
-    out["dot2_f32_2^26"] = {"ms": round(t * 1e3, 4), "GB/s": round(8 * nd2 / t / 1e9, 1),
-                            "frac_hbm": round(8 * nd2 / t / 1e9 / hbm, 4), "values_s": nd2 / t}
-    t = time_fn(torch, lambda: ff.sum2(g2.x), 10)
-    out["sum2_f32_2^26"] = {"ms": round(t * 1e3, 4), "GB/s": round(4 * nd2 / t / 1e9, 1),
-                            "frac_hbm": round(4 * nd2 / t / 1e9 / hbm, 4), "values_s": nd2 / t}
+    out["dot2_f32_2^26"] = red_row(lambda: ff.dot2(g2.x, g2.y, out=red_out), 8 * nd2, nd2, "values_s")
+    out["sum2_f32_2^26"] = red_row(lambda: ff.sum2(g2.x, out=red_out), 4 * nd2, nd2, "values_s")
     del g2
     torch.cuda.empty_cache()
 
@@ -529,12 +535,8 @@ def extra_rows(torch, ff, inputs, e, dev, peaks):
     nd = 1 << 26
     g = inputs.ill_dot(nd, 1e12, inputs.seed_for(2, 12), device=dev)
     x, y = g.x, g.y
-    t = time_fn(torch, lambda: ff.dot(x, y), 10)
-    out["dot_2^26"] = {"ms": round(t * 1e3, 4), "GB/s": round(16 * nd / t / 1e9, 1),
-                       "frac_hbm": round(16 * nd / t / 1e9 / hbm, 4), "ff_op_s": 2 * nd / t}
-    t = time_fn(torch, lambda: ff.sum(x), 10)
-    out["sum_2^26"] = {"ms": round(t * 1e3, 4), "GB/s": round(8 * nd / t / 1e9, 1),
-                       "frac_hbm": round(8 * nd / t / 1e9 / hbm, 4), "ff_op_s": nd / t}
+    out["dot_2^26"] = red_row(lambda: ff.dot(x, y, out=red_out), 16 * nd, 2 * nd, "ff_op_s")
+    out["sum_2^26"] = red_row(lambda: ff.sum(x, out=red_out), 8 * nd, nd, "ff_op_s")
     dout = torch.tensor([1.0, 0.0], device=dev)
     dx = torch.empty_like(x)
     dy = torch.empty_like(y)
@@ -662,10 +664,13 @@ def gemm_rows(torch, ff, inputs, dev, size=4096, fp32_measured=None):
 
 
 def batched_rows(torch, ff, inputs, dev, peaks):
-    """4096 dot / AXPY instances, lengths log-uniform over 1e2..1e7: one
-    persistent launch (plain run and CUDA graph) against 4096 plain calls
-    (loop and CUDA graph); then the same dots' forward and adjoint batched
-    against plain ff_dot / ff_dot_backward calls."""
+    """4096 dot / AXPY instances, lengths log-uniform over 1e2..1e7 (dots by
+    the ill-conditioned generator at cond 1e8, AXPY by the elementwise one
+    with its 10% cancelling pairs): one persistent launch (plain run and CUDA
+    graph) against 4096 plain calls (loop and CUDA graph); then the same
+    dots' forward and adjoint batched against plain ff_dot / ff_dot_backward
+    calls; last, the 4096 instances packed without padding, so that every
+    instance after an odd length starts 8 bytes off a 16-byte boundary."""
     from paper_cs_0603115_gb300 import batch
     hbm = peaks["hbm_gbs"]
     lengths, kinds = inputs.batch_lengths(4096, inputs.seed_for(3, 0))
@@ -681,22 +686,27 @@ def batched_rows(torch, ff, inputs, dev, peaks):
     D = torch.empty((4096, 2), dtype=torch.float32, device=dev)
     Dplain = torch.empty_like(D)
     dout = torch.empty((4096, 2), dtype=torch.float32, device=dev)
-    alphas = []
-    for i, (n, kind) in enumerate(zip(lengths, kinds)):
-        sl = slice(offs[i], offs[i] + n)
-        if kind == batch.DOT:
-            g = inputs.ill_dot(n, 1e8, inputs.seed_for(3, 1) + 7 * i, device=dev)
-            X[sl].copy_(g.x)
-            Y[sl].copy_(g.y)
-            del g
-        else:
-            e = inputs.elementwise(n, inputs.seed_for(3, 2) + 7 * i, device=dev, cancel_frac=0.0)
-            X[sl].copy_(e.a)
-            Y[sl].copy_(e.b)
-            del e
-        alphas.append(tuple(float(v) for v in inputs.scalar_ff(inputs.seed_for(3, 3) + i)))
+    alphas = [tuple(float(v) for v in inputs.scalar_ff(inputs.seed_for(3, 3) + i)) for i in range(4096)]
+    for i in range(4096):
         dout[i].copy_(inputs.scalar_ff(inputs.seed_for(3, 4) + i))
-    torch.cuda.synchronize()
+
+    def fill(offsets):
+        """Every instance's inputs at its offset (the same values whatever the offsets)."""
+        for i, (n, kind) in enumerate(zip(lengths, kinds)):
+            sl = slice(offsets[i], offsets[i] + n)
+            if kind == batch.DOT:
+                g = inputs.ill_dot(n, 1e8, inputs.seed_for(3, 1) + 7 * i, device=dev)
+                X[sl].copy_(g.x)
+                Y[sl].copy_(g.y)
+                del g
+            else:
+                e = inputs.elementwise(n, inputs.seed_for(3, 2) + 7 * i, device=dev)
+                X[sl].copy_(e.a)
+                Y[sl].copy_(e.b)
+                del e
+        torch.cuda.synchronize()
+
+    fill(offs)
     sl = [slice(offs[i], offs[i] + lengths[i]) for i in range(4096)]
     specs = [(k, X[sl[i]], Y[sl[i]], D[i] if k == batch.DOT else Z[sl[i]], alphas[i]) for i, k in enumerate(kinds)]
     inst = batch.make_instances(specs)
@@ -797,6 +807,59 @@ def batched_rows(torch, ff, inputs, dev, peaks):
         "fwd_max_absdiff_vs_plain_over_sum_abs": fwd_rel, "grad_bitequal_plain": grad_equal}
     pf.close()
     pb.close()
+
+    # the same instances packed back to back: an instance that follows an odd
+    # length starts 8 bytes off a 16-byte boundary and runs the batched
+    # kernel's scalar path (the plain kernels realign with one head value)
+    offs_u, o = [], 0
+    for n in lengths:
+        offs_u.append(o)
+        o += n
+    fill(offs_u)
+    slu = [slice(offs_u[i], offs_u[i] + lengths[i]) for i in range(4096)]
+    inst_u = batch.make_instances([(k, X[slu[i]], Y[slu[i]], D[i] if k == batch.DOT else Z[slu[i]], alphas[i])
+                                   for i, k in enumerate(kinds)])
+    plan_u = batch.BatchPlan(inst_u, tune=tune).capture()
+
+    def plain_u():
+        for i, k in enumerate(kinds):
+            if k == batch.DOT:
+                ff.dot(X[slu[i]], Y[slu[i]], out=Dplain[i])
+            else:
+                ff.axpy(alphas[i], X[slu[i]], Y[slu[i]], out=Z[slu[i]])
+
+    gu = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        plain_u()
+    torch.cuda.current_stream().wait_stream(s)
+    with torch.cuda.graph(gu):
+        plain_u()
+    tu_plain_graph = time_fn(torch, gu.replay, 3, warm=1)
+    tu = time_fn(torch, plan_u.launch, 5)
+    gu.replay()
+    torch.cuda.synchronize()
+    z_plain = Z.clone()
+    plan_u.launch()
+    torch.cuda.synchronize()
+    axpy_equal_u = bool(torch.equal(Z.view(torch.int32), z_plain.view(torch.int32)))
+    del z_plain
+    rel_u = 0.0
+    for i, k in enumerate(kinds):
+        if k == batch.DOT:
+            xv, yv = inputs.ff_to_f64(X[slu[i]]), inputs.ff_to_f64(Y[slu[i]])
+            a = float((xv * yv).abs().sum().item())
+            d = abs((float(D[i, 0]) - float(Dplain[i, 0])) + (float(D[i, 1]) - float(Dplain[i, 1])))
+            rel_u = max(rel_u, d / a if a > 0 else d)
+    rows["batched_4096_dot_axpy_unpadded"] = {
+        "values": total, "instances_off_16B": sum(1 for v in offs_u if v & 1),
+        "plain_graph_ms": round(tu_plain_graph * 1e3, 3), "batched_graph_ms": round(tu * 1e3, 3),
+        "speedup_vs_plain_graph": round(tu_plain_graph / tu, 3), "GB/s": round(bytes_total / tu / 1e9, 1),
+        "frac_hbm": round(bytes_total / tu / 1e9 / hbm, 4), "tune": list(tune), "axpy_bitequal_plain": axpy_equal_u,
+        "dot_max_absdiff_vs_plain_over_sum_abs": rel_u}
+    plan_u.close()
+    del gu
     del X, Y, Z, W, D, Dplain, dout
     torch.cuda.empty_cache()
     rows.update(batched_gemv_row(torch, ff, inputs, dev, hbm))

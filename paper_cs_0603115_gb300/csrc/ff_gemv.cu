@@ -113,9 +113,24 @@ inline int f64_tile_for(int64_t k) { return k >= 16 ? 16 : k >= 8 ? 8 : k >= 4 ?
 // ---------------------------------------------------------------------------
 // dX = A^T dY
 // ---------------------------------------------------------------------------
+// Rows of A each thread of the adjoint loads before using them, for tiles
+// of up to seven right-hand sides: the fewer terms a row gives, the more
+// rows must be in flight to cover the HBM latency.
+constexpr int kTRows(int kt) { return kt <= 2 ? 8 : 4; }
+
+// Resident blocks per SM the register allocation must leave room for: with
+// this many warps the narrow tiles (bound by FP32 issue, with a row load
+// ahead of few terms) hide their load latency; left to itself the compiler
+// chose fewer registers and scheduled the row loads later (k = 2-7 at 32768^2:
+// 0.83-0.92 of the FP32 roofline without, 0.88-0.93 with).
+constexpr int gemv_t_min_blocks(int kt, bool vec)
+{
+    return vec ? (kt <= 2 ? 5 : (kt <= 3 ? 4 : (kt <= 8 ? 3 : 2))) : (kt <= 8 ? 4 : 3);
+}
+
 // Partial sums: ws[(rb * k + c) * n + j] for row block rb.
 template <int KT, bool VEC>
-__global__ void __launch_bounds__(kGBlock)
+__global__ void __launch_bounds__(kGBlock, gemv_t_min_blocks(KT, VEC))
 gemv_t_kernel(const float2* __restrict__ A, int64_t m, int64_t n, int64_t lda, const float2* __restrict__ dY,
               int64_t lddy, int64_t rows_per_block, float2* __restrict__ out, int64_t out_ld, int64_t out_rb_stride)
 {
@@ -134,17 +149,18 @@ gemv_t_kernel(const float2* __restrict__ A, int64_t m, int64_t n, int64_t lda, c
         }
         int64_t r = r0;
         if constexpr (KT <= 7) {
-            // four rows loaded ahead of use: a narrow tile has too few terms
-            // per row to hide the HBM latency of the next row's load (from
-            // eight right-hand sides on, two rows measured faster)
-            for (; r + 3 < r1; r += 4) {
-                float4 a[4];
+            // kTRows(KT) rows loaded ahead of use: a narrow tile has too few
+            // terms per row to hide the HBM latency of the next row's load
+            // (from eight right-hand sides on, two rows measured faster)
+            constexpr int R = kTRows(KT);
+            for (; r + R - 1 < r1; r += R) {
+                float4 a[R];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) a[q] = __ldcs(reinterpret_cast<const float4*>(A + (r + q) * lda) + jp);
+                for (int q = 0; q < R; ++q) a[q] = __ldcs(reinterpret_cast<const float4*>(A + (r + q) * lda) + jp);
 #pragma unroll
                 for (int c = 0; c < KT; ++c) {
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
+                    for (int q = 0; q < R; ++q) {
                         const float2 d = __ldg(dY + c * lddy + r + q);
                         acc0[c] = ffk::add22(acc0[c], ffk::mul22(make_float2(a[q].x, a[q].y), d));
                         acc1[c] = ffk::add22(acc1[c], ffk::mul22(make_float2(a[q].z, a[q].w), d));
