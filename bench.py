@@ -988,6 +988,9 @@ def run_case(args):
         dout = torch.tensor([1.0, 0.0], device=dev)
         fn = {"dot": lambda: ff.dot(x, y), "sum": lambda: ff.sum(x),
               "dot_backward": lambda: ff.dot_backward(dout, x, y)}[args.case]
+    elif args.case in ("dot2", "sum2"):
+        g = inputs.ill_dot_f32(n, 1e12, inputs.seed_for(5, 12), device=dev)
+        fn = (lambda: ff.dot2(g.x, g.y)) if args.case == "dot2" else (lambda: ff.sum2(g.x))
     elif args.case == "batch":
         # 256 dot / AXPY instances, lengths log-uniform over 1e2..1e6 (a small
         # sample of the 4096-instance workload), one persistent launch
@@ -1025,7 +1028,9 @@ def run_case(args):
             oa += mm * nn
             ox += nn
             oy += mm
-        plan = batch.BatchPlan(batch.make_instances(specs), tune=(256, 128, 4, 2))
+        # the launch shape the autotuner picks for bench.py's 1024-GEMV batch:
+        # 128-thread blocks, as many resident as fit
+        plan = batch.BatchPlan(batch.make_instances(specs), tune=(128, 16, 0, 2))
         fn = plan.run
     elif args.case == "gemm":
         # --n is the matrix order here: C (n x n) = A (n x n) B (n x n)

@@ -305,7 +305,9 @@ typedef enum ff_batch_kind {
  *             values, out m values; each row is reduced like a DOT instance.
  * All pointers are device pointers owned by the caller and must stay valid
  * while any plan or graph built from the instance is used; unused pointers
- * may be NULL. */
+ * may be NULL.  Arrays need 8-byte alignment; an instance whose arrays all
+ * share their offset modulo 16 bytes runs on 16-byte access (after one
+ * value when that offset is 8), others on 8-byte access. */
 typedef struct ff_batch_instance {
     int32_t kind;
     int32_t reserved;

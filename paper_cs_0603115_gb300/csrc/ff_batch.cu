@@ -17,8 +17,14 @@
 //   per tile (R chosen at plan time so that a tile holds about 16K values);
 //   the exact lane and chunk order is given at gemv_rows_tile_body.  Longer
 //   GEMV rows become dot records (row r of the matrix with the vector).
+//   Access: 16-byte vectors of two values when all of a record's arrays
+//   start on a 16-byte boundary; when they all start 8 bytes past one,
+//   thread 0 takes each tile's first value on its own and the rest of the
+//   tile runs on 16-byte vectors; otherwise 8-byte loads.
 //   dot tile:  each thread accumulates its values left to right with
-//              Add22(acc, Mul22(x_i, y_i)); the block combines threads with
+//              Add22(acc, Mul22(x_i, y_i)) (thread 0 the tile's first value
+//              first when it is taken on its own, and an odd last value
+//              last); the block combines threads with
 //              the shuffle-down Add22 tree of ff_dot and stores the tile's
 //              partial; the tile that finishes its instance last (atomic
 //              counter per instance) adds the instance's tile partials in
@@ -59,7 +65,7 @@ struct DevInst {
     int64_t first_tile;
     int32_t ntiles;
     int32_t kind;
-    int32_t vec;
+    int32_t vec;   // 1: 16-byte access; 2: one value, then 16-byte access; 0: 8-byte access
     int32_t rows_per_warp;  // GEMV rows: rows each warp reduces per tile
 };
 
@@ -204,12 +210,18 @@ batch_kernel(const DevInst* __restrict__ insts, const Tile* __restrict__ tiles, 
         }
         const int64_t s0 = tl.start;
         const int64_t s1 = min(s0 + static_cast<int64_t>(BLOCK) * PPT, I.n);
+        // vec == 2: the instance's arrays all start 8 bytes past a 16-byte
+        // boundary, and so does every tile (tiles hold an even number of
+        // values); thread 0 takes the tile's first value on its own and the
+        // rest runs on 16-byte access
+        const int64_t h = (I.vec == 2 && s1 > s0) ? 1 : 0;
         if (I.kind == FF_BATCH_DOT) {
             float2 acc = make_float2(0.0f, 0.0f);
             if (I.vec) {
-                const float4* xv = reinterpret_cast<const float4*>(I.x + s0);
-                const float4* yv = reinterpret_cast<const float4*>(I.y + s0);
-                const int64_t len = s1 - s0;
+                if (h && threadIdx.x == 0) acc = ffk::add22(acc, ffk::mul22(I.x[s0], I.y[s0]));
+                const float4* xv = reinterpret_cast<const float4*>(I.x + s0 + h);
+                const float4* yv = reinterpret_cast<const float4*>(I.y + s0 + h);
+                const int64_t len = s1 - s0 - h;
                 const int64_t nch = len >> 1;
 #pragma unroll 1
                 for (int j0 = 0; j0 < CH; j0 += U) {
@@ -266,11 +278,15 @@ batch_kernel(const DevInst* __restrict__ insts, const Tile* __restrict__ tiles, 
         } else if (I.kind == FF_BATCH_DOT_GRAD) {
             const float2 d = __ldg(I.dout);
             if (I.vec) {
-                const float4* xv = reinterpret_cast<const float4*>(I.x + s0);
-                const float4* yv = reinterpret_cast<const float4*>(I.y + s0);
-                float4* dxv = reinterpret_cast<float4*>(I.out + s0);
-                float4* dyv = reinterpret_cast<float4*>(I.out2 + s0);
-                const int64_t len = s1 - s0;
+                if (h && threadIdx.x == 0) {
+                    I.out[s0] = ffk::mul22(d, I.y[s0]);
+                    I.out2[s0] = ffk::mul22(d, I.x[s0]);
+                }
+                const float4* xv = reinterpret_cast<const float4*>(I.x + s0 + h);
+                const float4* yv = reinterpret_cast<const float4*>(I.y + s0 + h);
+                float4* dxv = reinterpret_cast<float4*>(I.out + s0 + h);
+                float4* dyv = reinterpret_cast<float4*>(I.out2 + s0 + h);
+                const int64_t len = s1 - s0 - h;
                 const int64_t nch = len >> 1;
 #pragma unroll 1
                 for (int j0 = 0; j0 < CH; j0 += U) {
@@ -314,10 +330,11 @@ batch_kernel(const DevInst* __restrict__ insts, const Tile* __restrict__ tiles, 
         } else {
             const float2 al = I.alpha;
             if (I.vec) {
-                const float4* xv = reinterpret_cast<const float4*>(I.x + s0);
-                const float4* yv = reinterpret_cast<const float4*>(I.y + s0);
-                float4* zv = reinterpret_cast<float4*>(I.out + s0);
-                const int64_t len = s1 - s0;
+                if (h && threadIdx.x == 0) I.out[s0] = ffk::add22(ffk::mul22(al, I.x[s0]), I.y[s0]);
+                const float4* xv = reinterpret_cast<const float4*>(I.x + s0 + h);
+                const float4* yv = reinterpret_cast<const float4*>(I.y + s0 + h);
+                float4* zv = reinterpret_cast<float4*>(I.out + s0 + h);
+                const int64_t len = s1 - s0 - h;
                 const int64_t nch = len >> 1;
 #pragma unroll 1
                 for (int j0 = 0; j0 < CH; j0 += U) {
@@ -358,9 +375,12 @@ batch_kernel(const DevInst* __restrict__ insts, const Tile* __restrict__ tiles, 
 
 // Kernel for plans whose records are all GEMV rows: the same tile walk and
 // row reduction, without the other paths, so that it needs few registers and
-// keeps many warps resident (the rows are latency-bound).
+// keeps many warps resident: the rows are latency-bound (two 16-byte loads
+// of A in flight per lane), so the register budget is set for a full SM of
+// 64 warps (1024-GEMV batch: 0.86 of the HBM rate at 48 registers, 0.92 at
+// 32).
 template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK)
+__global__ void __launch_bounds__(BLOCK, 2048 / BLOCK)
 batch_gemv_kernel(const DevInst* __restrict__ insts, const Tile* __restrict__ tiles, int64_t ntiles,
                   float2* __restrict__, unsigned* __restrict__, unsigned long long* __restrict__ next)
 {
@@ -531,9 +551,17 @@ ff_status ff_batch_plan_create(const ff_batch_instance* inst, int count, const f
             total += b.m * b.n;
             continue;
         }
-        d.vec = (ffh::aligned(b.x, 16) && ffh::aligned(b.y, 16) &&
-                 (b.kind == FF_BATCH_DOT || ffh::aligned(b.out, 16)) &&
-                 (b.kind != FF_BATCH_DOT_GRAD || ffh::aligned(b.out2, 16))) ? 1 : 0;
+        // 16-byte access when every array the record reads or writes value
+        // by value starts on a 16-byte boundary, or when all of them start 8
+        // bytes past one (a one-value head realigns each tile); otherwise
+        // 8-byte access
+        {
+            const uintptr_t m = reinterpret_cast<uintptr_t>(b.x) & 15u;
+            bool same = (reinterpret_cast<uintptr_t>(b.y) & 15u) == m;
+            if (b.kind != FF_BATCH_DOT) same = same && (reinterpret_cast<uintptr_t>(b.out) & 15u) == m;
+            if (b.kind == FF_BATCH_DOT_GRAD) same = same && (reinterpret_cast<uintptr_t>(b.out2) & 15u) == m;
+            d.vec = !same ? 0 : (m == 0 ? 1 : (m == 8 ? 2 : 0));
+        }
         // a dot of length 0 still needs one tile to write its (0, 0)
         const int64_t nt = b.n > 0 ? (b.n + tile - 1) / tile : (b.kind == FF_BATCH_DOT ? 1 : 0);
         if (nt > INT32_MAX) return FF_ERR_INVALID_ARG;

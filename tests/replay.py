@@ -236,16 +236,20 @@ def _batch_block_tree(acc, block):
     return s[0]
 
 
-def batch_dot_replay(x, y, block: int, ppt: int, vec: bool):
+def batch_dot_replay(x, y, block: int, ppt: int, vec):
     """A DOT instance of the batched kernel (ff_batch.cu): tiles of
     block x ppt values; in a tile, thread t accumulates from (0, 0) the
-    two-value chunks t, t + block, ... (vec; with an odd tile length thread 0
-    then adds the last value) or the values t, t + block, ... (not vec), each
-    term Add22(acc, Mul22(x_i, y_i)); the block tree combines the threads;
-    one tile writes its value, several tiles are combined by the last one:
-    thread p adds the tile partials p, p + block, ... from (0, 0), then the
-    block tree.  Returns the (2,) result."""
+    two-value chunks t, t + block, ... (vec 1 or True: 16-byte access; with an
+    odd tile length thread 0 then adds the last value), or thread 0 first
+    adds the tile's first value on its own and the chunks start one value
+    later (vec 2: x and y both 8 bytes past a 16-byte boundary), or the
+    values t, t + block, ... (vec 0 or False), each term Add22(acc,
+    Mul22(x_i, y_i)); the block tree combines the threads; one tile writes
+    its value, several tiles are combined by the last one: thread p adds the
+    tile partials p, p + block, ... from (0, 0), then the block tree.
+    Returns the (2,) result."""
     add = lambda a, b: oracle.add22(np.ascontiguousarray(a), np.ascontiguousarray(b))
+    mode = int(vec)
     x = np.ascontiguousarray(x, np.float32)
     y = np.ascontiguousarray(y, np.float32)
     n = x.shape[0]
@@ -256,10 +260,14 @@ def batch_dot_replay(x, y, block: int, ppt: int, vec: bool):
     for t in range(nt):
         s0, s1 = t * tile, min((t + 1) * tile, n)
         T = terms[s0:s1]
-        ln = s1 - s0
         acc = np.zeros((block, 2), f32)
         tid = np.arange(block)
-        if vec:
+        if mode:
+            h = 1 if (mode == 2 and s1 > s0) else 0
+            if h:
+                acc[0] = add(acc[0:1], T[0:1])[0]
+            T = T[h:]
+            ln = s1 - s0 - h
             nch = ln // 2
             for j in range(ppt // 2):
                 c = tid + j * block
@@ -270,6 +278,7 @@ def batch_dot_replay(x, y, block: int, ppt: int, vec: bool):
             if ln & 1:
                 acc[0] = add(acc[0:1], T[ln - 1:ln])[0]
         else:
+            ln = s1 - s0
             for j in range(ppt):
                 i = tid + j * block
                 ok = i < ln

@@ -32,7 +32,11 @@ def build_case(lengths, kinds, seed):
     from paper_cs_0603115_gb300 import batch
     specs, keep = [], []
     for i, (n, kind) in enumerate(zip(lengths, kinds)):
-        mis = (i % 5 == 3)   # every fifth instance starts 8 bytes off a 16-byte boundary
+        # every fifth instance starts 8 bytes off a 16-byte boundary; of
+        # those, every other one has its outputs off the boundary too (16-byte
+        # access after one value), the others aligned outputs (8-byte access)
+        mis = (i % 5 == 3)
+        out_mis = mis and (i % 10 == 8)
         if kind == batch.DOT:
             g = inputs.ill_dot(max(n, 4), 1e8, seed + i)
             x, y = g.x[:n], g.y[:n]
@@ -44,7 +48,11 @@ def build_case(lengths, kinds, seed):
         xd.copy_(x)
         yd.copy_(y)
         alpha = inputs.scalar_ff(seed + 1000 + i)
-        out = torch.full((2,) if kind == batch.DOT else (n, 2), float("nan"), dtype=torch.float32, device=DEV)
+        if kind == batch.DOT:
+            out = torch.full((2,), float("nan"), dtype=torch.float32, device=DEV)
+        else:
+            out = torch.full((n + 1, 2), float("nan"), dtype=torch.float32,
+                             device=DEV)[int(out_mis):int(out_mis) + n]
         if kind == batch.DOT_GRAD:
             out2 = torch.full((n + 1, 2), float("nan"), dtype=torch.float32, device=DEV)[int(mis):int(mis) + n]
             dout = alpha.to(DEV)
@@ -238,22 +246,28 @@ def test_batch_gemv_only_plan_bitexact(tune):
 
 @pytest.mark.parametrize("tune", [(256, 32, 0, 4), (128, 16, 0, 2), (512, 64, 2, 4), (256, 128, 4, 2)])
 def test_batch_dot_bitexact_vs_order_replay(tune):
-    """DOT instances of a batched plan, aligned (16-byte access) and
-    misaligned, one tile and many: bit for bit against the replay of the
-    kernel's tile, thread and block order for this tune."""
+    """DOT instances of a batched plan, aligned (16-byte access), both
+    arrays 8 bytes off a 16-byte boundary (a one-value head, then 16-byte
+    access) and of mixed alignment (8-byte access), one tile and many: bit
+    for bit against the replay of the kernel's tile, thread and block order
+    for this tune."""
     from paper_cs_0603115_gb300 import batch
     import replay
-    lengths = [0, 1, 7, 8191, 8192, 8193, 100001, 33]
-    g = inputs.ill_dot(sum(lengths) + 2 * len(lengths) + 2, 1e8, inputs.seed_for(3, 60))
+    lengths = [0, 1, 7, 8191, 8192, 8193, 100001, 33, 2, 4097, 65537, 3]
+    g = inputs.ill_dot(sum(lengths) + 4 * len(lengths) + 4, 1e8, inputs.seed_for(3, 60))
     X, Y = g.x.to(DEV), g.y.to(DEV)
     D = torch.full((len(lengths), 2), float("nan"), device=DEV)
     specs, keep, o = [], [], 0
     for i, n in enumerate(lengths):
-        off = o + (i % 2)            # odd instances start 8 bytes past a 16-byte boundary
-        xs, ys = X[off:off + n], Y[off:off + n]
+        # instance i % 3: 0 both aligned (16-byte access), 1 both 8 bytes
+        # past a boundary (one value, then 16-byte access), 2 only y past a
+        # boundary (8-byte access)
+        offx = o + (i % 3 == 1)
+        offy = o + (i % 3 >= 1)
+        xs, ys = X[offx:offx + n], Y[offy:offy + n]
         specs.append((batch.DOT, xs, ys, D[i], None))
-        keep.append((xs.cpu().numpy(), ys.cpu().numpy(), i % 2 == 0))
-        o = off + n + 2
+        keep.append((xs.cpu().numpy(), ys.cpu().numpy(), (1, 2, 0)[i % 3]))
+        o = max(offx, offy) + n + 2
         o += o % 2
     plan = batch.BatchPlan(batch.make_instances(specs), tune=tune)
     plan.run()
