@@ -347,10 +347,13 @@ __device__ __forceinline__ float2 add22_from_zero(float2 t, bool warp_fast)
 // values of kTChunk rows at a time in shared memory, where one 16-byte read
 // gives both rows of a pair for one right-hand side.  Every element is
 // Add22((0, 0), term_0), then Add22 of terms 1 .. k-1, in order (the first
-// step through add22_from_zero, bit-identical).  Lanes past the last column
-// pair work on the last pair and do not store, so that every lane of a warp
-// takes part in the vote and every thread reaches the block barriers.
-template <int KT>
+// step through add22_from_zero, bit-identical).  With ACC the elements
+// continue from the values dA holds (the partial sums of the right-hand
+// sides before these k: a second pass for 8 < k <= 16), adding terms 0 .. k-1
+// in order.  Lanes past the last column pair work on the last pair and do
+// not store, so that every lane of a warp takes part in the vote and every
+// thread reaches the block barriers.
+template <int KT, bool ACC>
 __global__ void __launch_bounds__(kGBlock)
 gemv_dA_small_kernel(const float2* __restrict__ dY, int64_t m, int64_t lddy, const float2* __restrict__ X, int64_t n,
                      int64_t ldx, float2* __restrict__ dA, int64_t ldda, int64_t rpb)
@@ -368,6 +371,7 @@ gemv_dA_small_kernel(const float2* __restrict__ dY, int64_t m, int64_t lddy, con
         xl[c] = make_float2(v.x, v.y);
         xh[c] = make_float2(v.z, v.w);
     }
+    constexpr int C0 = ACC ? 0 : 1;   // first term added by the loop below
     const int64_t r0 = static_cast<int64_t>(blockIdx.y) * rpb;
     const int64_t r1 = r0 + rpb < m ? r0 + rpb : m;
     const int64_t rp = r0 + ((r1 > r0 ? r1 - r0 : 0) & ~static_cast<int64_t>(1));   // end of the row pairs
@@ -382,18 +386,29 @@ gemv_dA_small_kernel(const float2* __restrict__ dY, int64_t m, int64_t lddy, con
         float4* row = reinterpret_cast<float4*>(dA + cb * ldda) + jp;
         const int64_t ldda4 = ldda >> 1;
         for (int lp = 0; lp < rows / 2; ++lp, row += 2 * ldda4) {
-            float4 d01 = sdy[0][lp];
-            const float2 t00 = ffk::mul22(make_float2(d01.x, d01.y), xl[0]);
-            const float2 t01 = ffk::mul22(make_float2(d01.x, d01.y), xh[0]);
-            const float2 t10 = ffk::mul22(make_float2(d01.z, d01.w), xl[0]);
-            const float2 t11 = ffk::mul22(make_float2(d01.z, d01.w), xh[0]);
-            const bool fast = __all_sync(0xffffffffu, from_zero_fast(t00) && from_zero_fast(t01) &&
-                                                          from_zero_fast(t10) && from_zero_fast(t11));
-            float2 a00 = add22_from_zero(t00, fast), a01 = add22_from_zero(t01, fast);
-            float2 a10 = add22_from_zero(t10, fast), a11 = add22_from_zero(t11, fast);
+            float2 a00, a01, a10, a11;
+            if constexpr (ACC) {
+                const float4 p0 = __ldcs(row), p1 = __ldcs(row + ldda4);
+                a00 = make_float2(p0.x, p0.y);
+                a01 = make_float2(p0.z, p0.w);
+                a10 = make_float2(p1.x, p1.y);
+                a11 = make_float2(p1.z, p1.w);
+            } else {
+                const float4 d01 = sdy[0][lp];
+                const float2 t00 = ffk::mul22(make_float2(d01.x, d01.y), xl[0]);
+                const float2 t01 = ffk::mul22(make_float2(d01.x, d01.y), xh[0]);
+                const float2 t10 = ffk::mul22(make_float2(d01.z, d01.w), xl[0]);
+                const float2 t11 = ffk::mul22(make_float2(d01.z, d01.w), xh[0]);
+                const bool fast = __all_sync(0xffffffffu, from_zero_fast(t00) && from_zero_fast(t01) &&
+                                                              from_zero_fast(t10) && from_zero_fast(t11));
+                a00 = add22_from_zero(t00, fast);
+                a01 = add22_from_zero(t01, fast);
+                a10 = add22_from_zero(t10, fast);
+                a11 = add22_from_zero(t11, fast);
+            }
 #pragma unroll
-            for (int c = 1; c < KT; ++c) {
-                d01 = sdy[c][lp];
+            for (int c = C0; c < KT; ++c) {
+                const float4 d01 = sdy[c][lp];
                 const float2 d0 = make_float2(d01.x, d01.y), d1 = make_float2(d01.z, d01.w);
                 a00 = ffk::add22(a00, ffk::mul22(d0, xl[c]));
                 a01 = ffk::add22(a01, ffk::mul22(d0, xh[c]));
@@ -408,51 +423,81 @@ gemv_dA_small_kernel(const float2* __restrict__ dY, int64_t m, int64_t lddy, con
     }
     if (rp < r1) {  // the last row of an odd m
         const int64_t r = rp;
-        const float2 d = __ldg(dY + r);
-        const float2 t0 = ffk::mul22(d, xl[0]), t1 = ffk::mul22(d, xh[0]);
-        const bool fast = __all_sync(0xffffffffu, from_zero_fast(t0) && from_zero_fast(t1));
-        float2 a0 = add22_from_zero(t0, fast), a1 = add22_from_zero(t1, fast);
+        float4* row = reinterpret_cast<float4*>(dA + r * ldda) + jp;
+        float2 a0, a1;
+        if constexpr (ACC) {
+            const float4 p = __ldcs(row);
+            a0 = make_float2(p.x, p.y);
+            a1 = make_float2(p.z, p.w);
+        } else {
+            const float2 d = __ldg(dY + r);
+            const float2 t0 = ffk::mul22(d, xl[0]), t1 = ffk::mul22(d, xh[0]);
+            const bool fast = __all_sync(0xffffffffu, from_zero_fast(t0) && from_zero_fast(t1));
+            a0 = add22_from_zero(t0, fast);
+            a1 = add22_from_zero(t1, fast);
+        }
 #pragma unroll
-        for (int c = 1; c < KT; ++c) {
+        for (int c = C0; c < KT; ++c) {
             const float2 dc = __ldg(dY + c * lddy + r);
             a0 = ffk::add22(a0, ffk::mul22(dc, xl[c]));
             a1 = ffk::add22(a1, ffk::mul22(dc, xh[c]));
         }
-        if (store) __stcs(reinterpret_cast<float4*>(dA + r * ldda) + jp, make_float4(a0.x, a0.y, a1.x, a1.y));
+        if (store) __stcs(row, make_float4(a0.x, a0.y, a1.x, a1.y));
     }
 }
 
-// Widest k that ff_gemv_dA runs on gemv_dA_small_kernel (the GEMM kernel
-// takes larger k).
-constexpr int kDAMaxSmallK = 8;
+// Widest k that ff_gemv_dA runs on gemv_dA_small_kernel: one pass up to 8
+// right-hand sides, two passes (the second continuing from the stored sums)
+// up to 13; the GEMM kernel takes larger k (from k = 14 on it measured as
+// fast or faster at 32768^2).
+constexpr int kDAPass = 8;
+constexpr int kDAMaxSmallK = 13;
 
+template <bool ACC>
 const void* dA_small_ptr(int k)
 {
     switch (k) {
-    case 1: return reinterpret_cast<const void*>(&gemv_dA_small_kernel<1>);
-    case 2: return reinterpret_cast<const void*>(&gemv_dA_small_kernel<2>);
-    case 3: return reinterpret_cast<const void*>(&gemv_dA_small_kernel<3>);
-    case 4: return reinterpret_cast<const void*>(&gemv_dA_small_kernel<4>);
-    case 5: return reinterpret_cast<const void*>(&gemv_dA_small_kernel<5>);
-    case 6: return reinterpret_cast<const void*>(&gemv_dA_small_kernel<6>);
-    case 7: return reinterpret_cast<const void*>(&gemv_dA_small_kernel<7>);
-    default: return reinterpret_cast<const void*>(&gemv_dA_small_kernel<8>);
+    case 1: return reinterpret_cast<const void*>(&gemv_dA_small_kernel<1, ACC>);
+    case 2: return reinterpret_cast<const void*>(&gemv_dA_small_kernel<2, ACC>);
+    case 3: return reinterpret_cast<const void*>(&gemv_dA_small_kernel<3, ACC>);
+    case 4: return reinterpret_cast<const void*>(&gemv_dA_small_kernel<4, ACC>);
+    case 5: return reinterpret_cast<const void*>(&gemv_dA_small_kernel<5, ACC>);
+    case 6: return reinterpret_cast<const void*>(&gemv_dA_small_kernel<6, ACC>);
+    case 7: return reinterpret_cast<const void*>(&gemv_dA_small_kernel<7, ACC>);
+    default: return reinterpret_cast<const void*>(&gemv_dA_small_kernel<8, ACC>);
     }
 }
 
+template <bool ACC>
 void launch_dA_small(int k, dim3 grid, cudaStream_t s, const float2* dY, int64_t m, int64_t lddy, const float2* X,
                      int64_t n, int64_t ldx, float2* dA, int64_t ldda, int64_t rpb)
 {
     switch (k) {
-    case 1: gemv_dA_small_kernel<1><<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, dA, ldda, rpb); break;
-    case 2: gemv_dA_small_kernel<2><<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, dA, ldda, rpb); break;
-    case 3: gemv_dA_small_kernel<3><<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, dA, ldda, rpb); break;
-    case 4: gemv_dA_small_kernel<4><<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, dA, ldda, rpb); break;
-    case 5: gemv_dA_small_kernel<5><<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, dA, ldda, rpb); break;
-    case 6: gemv_dA_small_kernel<6><<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, dA, ldda, rpb); break;
-    case 7: gemv_dA_small_kernel<7><<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, dA, ldda, rpb); break;
-    default: gemv_dA_small_kernel<8><<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, dA, ldda, rpb); break;
+    case 1: gemv_dA_small_kernel<1, ACC><<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, dA, ldda, rpb); break;
+    case 2: gemv_dA_small_kernel<2, ACC><<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, dA, ldda, rpb); break;
+    case 3: gemv_dA_small_kernel<3, ACC><<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, dA, ldda, rpb); break;
+    case 4: gemv_dA_small_kernel<4, ACC><<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, dA, ldda, rpb); break;
+    case 5: gemv_dA_small_kernel<5, ACC><<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, dA, ldda, rpb); break;
+    case 6: gemv_dA_small_kernel<6, ACC><<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, dA, ldda, rpb); break;
+    case 7: gemv_dA_small_kernel<7, ACC><<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, dA, ldda, rpb); break;
+    default: gemv_dA_small_kernel<8, ACC><<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, dA, ldda, rpb); break;
     }
+}
+
+// Grid of one wave of resident blocks of `kern` (rounded down so that every
+// block is resident at once), block rows of an even number of rows.
+void dA_small_grid(const void* kern, int64_t m, int64_t n, int sm_count, dim3* grid, int64_t* rpb)
+{
+    const int64_t col_blocks = (n / 2 + kGBlock - 1) / kGBlock;
+    const int occ = ffh::occupancy(kern, kGBlock);
+    int64_t gy = static_cast<int64_t>(sm_count) * (occ > 0 ? occ : 1) / col_blocks;
+    if (gy > (m + 1) / 2) gy = (m + 1) / 2;
+    if (gy > 65535) gy = 65535;
+    if (gy < 1) gy = 1;
+    int64_t r = (m + gy - 1) / gy;
+    r += r & 1;
+    *rpb = r;
+    *grid = dim3(static_cast<unsigned>(col_blocks), static_cast<unsigned>((m + r - 1) / r));
 }
 
 // ---------------------------------------------------------------------------
@@ -630,32 +675,37 @@ ff_status ff_gemv_dA(const ff2* dY_, int64_t m, int64_t lddy, const ff2* X_, int
     auto* X = reinterpret_cast<const float2*>(X_);
     auto* dA = reinterpret_cast<float2*>(dA_);
     const bool vec = (n % 2 == 0) && (ldx % 2 == 0) && (ldda % 2 == 0) && ffh::aligned(X, 16) && ffh::aligned(dA, 16);
+    if (!vec && k > kDAPass) return ff_gemm(1, 0, m, n, k, dY_, lddy, X_, ldx, dA_, ldda, s);
     ffh::DeviceInfo di;
     const ff_status st = ffh::device_info(&di);
     if (st != FF_OK) return st;
-    // one wave of resident blocks (rounded down so that every block is
-    // resident at once)
-    const int64_t col_blocks = ((vec ? n / 2 : n) + kGBlock - 1) / kGBlock;
-    const void* kern = vec ? dA_small_ptr(static_cast<int>(k)) : reinterpret_cast<const void*>(&gemv_dA_scalar_kernel);
-    const int occ = ffh::occupancy(kern, kGBlock);
-    int64_t gy64 = static_cast<int64_t>(di.sm_count) * (occ > 0 ? occ : 1) / col_blocks;
     if (vec) {
-        // block rows of an even number of rows, every block row non-empty
-        if (gy64 > (m + 1) / 2) gy64 = (m + 1) / 2;
-        if (gy64 > 65535) gy64 = 65535;
-        if (gy64 < 1) gy64 = 1;
-        int64_t rpb = (m + gy64 - 1) / gy64;
-        rpb += rpb & 1;
-        gy64 = (m + rpb - 1) / rpb;
-        dim3 grid(static_cast<unsigned>((n / 2 + kGBlock - 1) / kGBlock), static_cast<unsigned>(gy64));
-        launch_dA_small(static_cast<int>(k), grid, s, dY, m, lddy, X, n, ldx, dA, ldda, rpb);
-    } else {
-        if (gy64 > m) gy64 = m;
-        if (gy64 > 65535) gy64 = 65535;
-        if (gy64 < 1) gy64 = 1;
-        dim3 grid(static_cast<unsigned>((n + kGBlock - 1) / kGBlock), static_cast<unsigned>(gy64));
-        gemv_dA_scalar_kernel<<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, k, dA, ldda);
+        // up to eight right-hand sides in one pass from (0, 0); more in two
+        // passes, the second continuing from the sums the first stored: a
+        // narrow second pass is bound by re-reading dA, so k < 12 is split in
+        // halves (32768^2: k = 9 as 8 + 1 measured 0.78 of the roofline, as
+        // 5 + 4 0.86; k = 10 as 5 + 5 0.87, as 6 + 4 0.86; k = 12 as 8 + 4
+        // 0.89, as 6 + 6 0.87)
+        const int k0 = static_cast<int>(k <= kDAPass ? k : (k >= 12 ? 8 : (k + 1) / 2));
+        dim3 grid;
+        int64_t rpb;
+        dA_small_grid(dA_small_ptr<false>(k0), m, n, di.sm_count, &grid, &rpb);
+        launch_dA_small<false>(k0, grid, s, dY, m, lddy, X, n, ldx, dA, ldda, rpb);
+        const ff_status st1 = ffh::check_launch();
+        if (st1 != FF_OK || k == k0) return st1;
+        const int k1 = static_cast<int>(k - k0);
+        dA_small_grid(dA_small_ptr<true>(k1), m, n, di.sm_count, &grid, &rpb);
+        launch_dA_small<true>(k1, grid, s, dY + k0 * lddy, m, lddy, X + k0 * ldx, n, ldx, dA, ldda, rpb);
+        return ffh::check_launch();
     }
+    const int64_t col_blocks = (n + kGBlock - 1) / kGBlock;
+    const int occ = ffh::occupancy(reinterpret_cast<const void*>(&gemv_dA_scalar_kernel), kGBlock);
+    int64_t gy64 = static_cast<int64_t>(di.sm_count) * (occ > 0 ? occ : 1) / col_blocks;
+    if (gy64 > m) gy64 = m;
+    if (gy64 > 65535) gy64 = 65535;
+    if (gy64 < 1) gy64 = 1;
+    dim3 grid(static_cast<unsigned>(col_blocks), static_cast<unsigned>(gy64));
+    gemv_dA_scalar_kernel<<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, k, dA, ldda);
     return ffh::check_launch();
 }
 
