@@ -446,7 +446,8 @@ def test_full_size_every_value_bitexact():
     torch.cuda.empty_cache()
 
 
-@pytest.mark.parametrize("m,n,k", [(37, 1000, 3), (20, 999, 2), (5, 64, 17), (1, 1, 1), (9, 33, 1)])
+@pytest.mark.parametrize("m,n,k", [(37, 1000, 3), (20, 999, 2), (5, 64, 17), (1, 1, 1), (9, 33, 1), (301, 1000, 2),
+                                   (64, 130, 7), (33, 2, 5), (17, 66, 1)])
 def test_gemv_bitexact_vs_order_replay(m, n, k):
     """ff_gemv bit for bit against the replay of its documented warp order."""
     import replay
