@@ -32,8 +32,14 @@ __device__ __forceinline__ float2 shfl_down2(float2 v, int off)
 // ---------------------------------------------------------------------------
 // Y = A X
 // ---------------------------------------------------------------------------
+// Resident blocks per SM that the 16-byte forward kernel of a KT-wide tile
+// is compiled for (0: the compiler's own choice).  Four for three to seven
+// right-hand sides (32768^2: +0.3-1.4%); for two, a budget for 6 or 8
+// blocks measured 4% and 14% slower than the compiler's own 48 registers.
+constexpr int gemv_min_blocks(int kt, bool vec) { return vec && kt >= 3 && kt <= 7 ? 4 : 0; }
+
 template <int KT, bool VEC>
-__global__ void __launch_bounds__(kGBlock)
+__global__ void __launch_bounds__(kGBlock, gemv_min_blocks(KT, VEC))
 gemv_kernel(const float2* __restrict__ A, int64_t m, int64_t n, int64_t lda, const float2* __restrict__ X,
             int64_t ldx, float2* __restrict__ Y, int64_t ldy)
 {
