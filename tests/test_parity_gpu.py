@@ -489,7 +489,8 @@ def test_gemv_result_does_not_depend_on_k(n):
 @pytest.mark.parametrize("m,n,k", [(33, 64, 1), (17, 129, 5), (64, 256, 64), (17, 129, 3), (301, 1000, 4),
                                    (300, 998, 2), (257, 66, 7), (256, 514, 8), (1000, 2050, 5), (999, 130, 6),
                                    (40, 20, 9), (301, 130, 12), (256, 66, 16), (33, 64, 15), (17, 129, 12),
-                                   (70, 50, 17), (100, 130, 13), (99, 64, 10), (129, 66, 11)])
+                                   (70, 50, 17), (100, 130, 13), (99, 64, 10), (129, 66, 11), (5, 2, 3),
+                                   (1, 4, 12), (2, 2, 1)])
 def test_gemv_dA_bitexact(m, n, k):
     gi = inputs.gemv(m, n, k, inputs.seed_for(4, 50 + k))
     dA = ff.gemv_dA(gpu(gi.dY), gpu(gi.X)).cpu().numpy()
