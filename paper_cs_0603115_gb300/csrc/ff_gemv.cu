@@ -138,9 +138,18 @@ ff_status launch_gemv_tile(const float2* A, int64_t m, int64_t n, int64_t lda, c
 
 // Tile width for the float-float kernels: up to seven right-hand sides in
 // one pass (one read of A: below eight the kernels are issue-bound only
-// once all k share the pass), else 8 or 16; any k takes at most one
-// remainder pass.  The FP64 baseline uses powers of two.
-inline int tile_for(int64_t k) { return k >= 16 ? 16 : k >= 8 ? 8 : static_cast<int>(k); }
+// once all k share the pass), else passes of eight.  Each pass of eight is
+// bound by FP32 issue several times over its read of A, so re-reading A per
+// pass costs nothing, and the eight-wide kernels issue better than sixteen-
+// wide ones (32768^2, k = 16-64: forward 0.93 -> 0.94, adjoint 0.90 -> 0.93
+// of the FP32 roofline).  Nine to eleven remaining right-hand sides are split
+// in two near halves rather than eight and a one- to three-wide pass that
+// would be bound by its read of A.  The FP64 baseline uses powers of two.
+// `k` is the number of right-hand sides not yet done.
+inline int tile_for(int64_t k)
+{
+    return k >= 12 ? 8 : (k > 8 ? static_cast<int>((k + 1) / 2) : static_cast<int>(k));
+}
 inline int f64_tile_for(int64_t k) { return k >= 16 ? 16 : k >= 8 ? 8 : k >= 4 ? 4 : k >= 2 ? 2 : 1; }
 
 // ---------------------------------------------------------------------------
@@ -181,10 +190,11 @@ gemv_t_kernel(const float2* __restrict__ A, int64_t m, int64_t n, int64_t lda, c
             acc1[c] = make_float2(0.0f, 0.0f);
         }
         int64_t r = r0;
-        if constexpr (KT <= 7) {
-            // kTRows(KT) rows loaded ahead of use: a narrow tile has too few
-            // terms per row to hide the HBM latency of the next row's load
-            // (from eight right-hand sides on, two rows measured faster)
+        {
+            // kTRows(KT) rows loaded ahead of use: a tile of at most eight
+            // right-hand sides has too few terms per row to hide the HBM
+            // latency of the next row's load (the loops below take the
+            // remaining rows)
             constexpr int R = kTRows(KT);
             for (; r + R - 1 < r1; r += R) {
                 float4 a[R];
@@ -277,8 +287,6 @@ void launch_gemv_t_tile(const float2* A, int64_t m, int64_t n, int64_t lda, cons
 const void* gemv_t_kernel_ptr(int kt, bool vec)
 {
     switch (kt) {
-    case 16: return vec ? reinterpret_cast<const void*>(&gemv_t_kernel<16, true>)
-                        : reinterpret_cast<const void*>(&gemv_t_kernel<16, false>);
     case 8: return vec ? reinterpret_cast<const void*>(&gemv_t_kernel<8, true>)
                        : reinterpret_cast<const void*>(&gemv_t_kernel<8, false>);
     case 7: return vec ? reinterpret_cast<const void*>(&gemv_t_kernel<7, true>)
@@ -595,7 +603,6 @@ ff_status ff_gemv(const ff2* A_, int64_t m, int64_t n, int64_t lda, const ff2* X
         const float2* Xc = X + c0 * ldx;
         float2* Yc = Y + c0 * ldy;
         switch (kt) {
-        case 16: st = launch_gemv_tile<16>(A, m, n, lda, Xc, ldx, Yc, ldy, vec, s); break;
         case 8: st = launch_gemv_tile<8>(A, m, n, lda, Xc, ldx, Yc, ldy, vec, s); break;
         case 7: st = launch_gemv_tile<7>(A, m, n, lda, Xc, ldx, Yc, ldy, vec, s); break;
         case 6: st = launch_gemv_tile<6>(A, m, n, lda, Xc, ldx, Yc, ldy, vec, s); break;
@@ -667,7 +674,6 @@ ff_status ff_gemv_t(const ff2* A_, int64_t m, int64_t n, int64_t lda, const ff2*
         const int64_t rb_stride = nrb > 1 ? k * n : 0;
         const int64_t mm = m > 0 ? m : 0;
         switch (kt) {
-        case 16: launch_gemv_t_tile<16>(A, mm, n, lda, dYc, lddy, rpb, nrb, out, out_ld, rb_stride, vec, s); break;
         case 8: launch_gemv_t_tile<8>(A, mm, n, lda, dYc, lddy, rpb, nrb, out, out_ld, rb_stride, vec, s); break;
         case 7: launch_gemv_t_tile<7>(A, mm, n, lda, dYc, lddy, rpb, nrb, out, out_ld, rb_stride, vec, s); break;
         case 6: launch_gemv_t_tile<6>(A, mm, n, lda, dYc, lddy, rpb, nrb, out, out_ld, rb_stride, vec, s); break;
