@@ -426,10 +426,19 @@ gemv_dA_small_kernel(const float2* __restrict__ dY, int64_t m, int64_t lddy, con
         __syncthreads();
         float4* row = reinterpret_cast<float4*>(dA + cb * ldda) + jp;
         const int64_t ldda4 = ldda >> 1;
+        float4 n0, n1;   // ACC: the stored sums of the next row pair, loaded one pair ahead
+        if constexpr (ACC) {
+            n0 = __ldcs(row);
+            n1 = __ldcs(row + ldda4);
+        }
         for (int lp = 0; lp < rows / 2; ++lp, row += 2 * ldda4) {
             float2 a00, a01, a10, a11;
             if constexpr (ACC) {
-                const float4 p0 = __ldcs(row), p1 = __ldcs(row + ldda4);
+                const float4 p0 = n0, p1 = n1;
+                if (lp + 1 < rows / 2) {
+                    n0 = __ldcs(row + 2 * ldda4);
+                    n1 = __ldcs(row + 3 * ldda4);
+                }
                 a00 = make_float2(p0.x, p0.y);
                 a01 = make_float2(p0.z, p0.w);
                 a10 = make_float2(p1.x, p1.y);
@@ -488,11 +497,12 @@ gemv_dA_small_kernel(const float2* __restrict__ dY, int64_t m, int64_t lddy, con
 }
 
 // Widest k that ff_gemv_dA runs on gemv_dA_small_kernel: one pass up to 8
-// right-hand sides, two passes (the second continuing from the stored sums)
-// up to 13; the GEMM kernel takes larger k (from k = 14 on it measured as
-// fast or faster at 32768^2).
+// right-hand sides, then passes that continue from the stored sums (loaded
+// one row pair ahead) up to 16; the GEMM kernel takes larger k (32768^2:
+// passes 0.92 against the GEMM route's 0.88-0.90 at k = 14-16, equal at
+// k = 20-24, 0.89-0.90 against 0.93-0.94 from k = 32).
 constexpr int kDAPass = 8;
-constexpr int kDAMaxSmallK = 13;
+constexpr int kDAMaxSmallK = 16;
 
 template <bool ACC>
 const void* dA_small_ptr(int k)
@@ -719,23 +729,28 @@ ff_status ff_gemv_dA(const ff2* dY_, int64_t m, int64_t lddy, const ff2* X_, int
     const ff_status st = ffh::device_info(&di);
     if (st != FF_OK) return st;
     if (vec) {
-        // up to eight right-hand sides in one pass from (0, 0); more in two
-        // passes, the second continuing from the sums the first stored: a
-        // narrow second pass is bound by re-reading dA, so k < 12 is split in
-        // halves (32768^2: k = 9 as 8 + 1 measured 0.78 of the roofline, as
-        // 5 + 4 0.86; k = 10 as 5 + 5 0.87, as 6 + 4 0.86; k = 12 as 8 + 4
-        // 0.89, as 6 + 6 0.87)
-        const int k0 = static_cast<int>(k <= kDAPass ? k : (k >= 12 ? 8 : (k + 1) / 2));
-        dim3 grid;
-        int64_t rpb;
-        dA_small_grid(dA_small_ptr<false>(k0), m, n, di.sm_count, &grid, &rpb);
-        launch_dA_small<false>(k0, grid, s, dY, m, lddy, X, n, ldx, dA, ldda, rpb);
-        const ff_status st1 = ffh::check_launch();
-        if (st1 != FF_OK || k == k0) return st1;
-        const int k1 = static_cast<int>(k - k0);
-        dA_small_grid(dA_small_ptr<true>(k1), m, n, di.sm_count, &grid, &rpb);
-        launch_dA_small<true>(k1, grid, s, dY + k0 * lddy, m, lddy, X + k0 * ldx, n, ldx, dA, ldda, rpb);
-        return ffh::check_launch();
+        // up to eight right-hand sides in one pass from (0, 0); more in
+        // passes of the widths tile_for gives (eight, and nine to eleven
+        // remaining as two halves), each continuing from the sums the
+        // previous ones stored: a narrow pass is bound by re-reading dA
+        // (32768^2: k = 9 as 8 + 1 measured 0.78 of the roofline, as 5 + 4
+        // 0.86; k = 12 as 8 + 4 0.89, as 6 + 6 0.87)
+        for (int64_t c0 = 0; c0 < k;) {
+            const int kt = tile_for(k - c0);
+            dim3 grid;
+            int64_t rpb;
+            if (c0 == 0) {
+                dA_small_grid(dA_small_ptr<false>(kt), m, n, di.sm_count, &grid, &rpb);
+                launch_dA_small<false>(kt, grid, s, dY, m, lddy, X, n, ldx, dA, ldda, rpb);
+            } else {
+                dA_small_grid(dA_small_ptr<true>(kt), m, n, di.sm_count, &grid, &rpb);
+                launch_dA_small<true>(kt, grid, s, dY + c0 * lddy, m, lddy, X + c0 * ldx, n, ldx, dA, ldda, rpb);
+            }
+            const ff_status stp = ffh::check_launch();
+            if (stp != FF_OK) return stp;
+            c0 += kt;
+        }
+        return FF_OK;
     }
     const int64_t col_blocks = (n + kGBlock - 1) / kGBlock;
     const int occ = ffh::occupancy(reinterpret_cast<const void*>(&gemv_dA_scalar_kernel), kGBlock);
