@@ -29,7 +29,11 @@ namespace {
 
 constexpr int kRBlock = 256;
 constexpr int kRWarps = kRBlock / 32;
-constexpr int kRMaxBlocksPerSm = 8;
+// Resident 256-thread blocks per SM at most: a read-only stream reaches a
+// higher DRAM rate with moderate residency than with every SM full (ff_sum
+// at 2^26 / 2^28: 0.97 / 1.02 of the measured copy rate with 8 blocks,
+// 0.995 / 1.06 with 6; ff_dot is held at 6 by its registers either way).
+constexpr int kRMaxBlocksPerSm = 6;
 constexpr size_t kPartialsOffset = 256;  // ticket at offset 0, partials at 256
 
 struct FFSum {
