@@ -635,3 +635,59 @@ def test_gemv_outputs_stay_inside_their_bounds(m, n, k):
     ff.gemv_dA(dY, X, out=view.view(m, n, 2))
     torch.cuda.synchronize()
     assert guards_intact(buf, m * n)
+
+
+# ---------------------------------------------------------------------------
+# GEMV family with leading dimensions larger than the sizes (through the C ABI)
+# ---------------------------------------------------------------------------
+
+def _padded(rows, cols, ld, src=None, fill=-7.25):
+    """A (rows, ld, 2) device buffer whose first `cols` columns hold `src`
+    (or stay `fill`) and whose padding columns hold `fill`."""
+    buf = torch.full((rows, ld, 2), fill, dtype=torch.float32, device=DEV)
+    if src is not None:
+        buf[:, :cols] = src.to(DEV)
+    return buf
+
+
+@pytest.mark.parametrize("m,n,k,pad", [(300, 258, 3, 2), (301, 130, 9, 4), (257, 66, 16, 2), (129, 98, 2, 1)])
+def test_gemv_family_with_leading_dimensions(m, n, k, pad):
+    """ff_gemv, ff_gemv_t and ff_gemv_dA on operands stored with row strides
+    (lda, ldx, lddy, ldy, lddx, ldda) `pad` values wider than the sizes: with
+    an even pad every kernel takes the same path as for packed operands and
+    gives the same bits; with an odd pad the 8-byte paths run, checked
+    against the replays of their order (ff_gemv, ff_gemv_t) and the oracle
+    (ff_gemv_dA, elementwise).  No padding value is touched."""
+    import ctypes
+    import replay
+    gi = inputs.gemv(m, n, k, inputs.seed_for(4, 150 + pad))
+    stream = torch.cuda.current_stream().cuda_stream
+    A = _padded(m, n, n + pad, gi.A)
+    X = _padded(k, n, n + pad, gi.X)
+    dY = _padded(k, m, m + pad, gi.dY)
+    Y = _padded(k, m, m + pad)
+    dX = _padded(k, n, n + pad)
+    dA = _padded(m, n, n + pad)
+    _lib.call("ff_gemv", A.data_ptr(), m, n, n + pad, X.data_ptr(), n + pad, k, Y.data_ptr(), m + pad, stream)
+    wsb = _lib.load().ff_gemv_t_workspace_bytes(m, n, k)
+    ws = torch.zeros(max(wsb, 256), dtype=torch.uint8, device=DEV)
+    _lib.call("ff_gemv_t", A.data_ptr(), m, n, n + pad, dY.data_ptr(), m + pad, k, dX.data_ptr(), n + pad,
+              ws.data_ptr(), ws.numel(), stream)
+    _lib.call("ff_gemv_dA", dY.data_ptr(), m, m + pad, X.data_ptr(), n, n + pad, k, dA.data_ptr(), n + pad, stream)
+    torch.cuda.synchronize()
+    for buf, cols in ((Y, m), (dX, n), (dA, n)):
+        tail = buf[:, cols:].cpu().numpy()
+        assert np.all(tail == np.float32(-7.25)), "padding overwritten"
+    Yg, dXg, dAg = Y[:, :m].cpu().numpy(), dX[:, :n].cpu().numpy(), dA[:, :n].cpu().numpy()
+    if pad % 2 == 0:
+        Ad, Xd, dYd = gpu(gi.A), gpu(gi.X), gpu(gi.dY)
+        same_bits(Yg, ff.gemv(Ad, Xd).cpu().numpy())
+        same_bits(dXg, ff.gemv_t(Ad, dYd).cpu().numpy())
+        same_bits(dAg, ff.gemv_dA(dYd, Xd).cpu().numpy())
+    else:
+        same_bits(Yg, replay.gemv_warp_replay(gi.A.numpy(), gi.X.numpy(), vec=False))
+        nrb, vec = ctypes.c_int64(), ctypes.c_int()
+        _lib.call("ff_gemv_t_launch_shape", A.data_ptr(), m, n, n + pad, k, ctypes.byref(nrb), ctypes.byref(vec))
+        assert vec.value == 0
+        same_bits(dXg, replay.gemv_t_replay(gi.A.numpy(), gi.dY.numpy(), nrb.value))
+        same_bits(dAg, oracle.gemv_dA(gi.dY.numpy(), gi.X.numpy()))
