@@ -255,7 +255,7 @@ FF_API ff_status ff_gemv_t_launch_shape(const ff2* A, int64_t m, int64_t n, int6
  * (0, 0) as the sum's definition says; its first Add22 (with the zero) is
  * formed in two additions when the term is a finite normalised pair (the
  * same bits), the full Add22 otherwise.  Up to k = 16 (with even n, ldx and
- * ldda and 16-byte aligned X and dA; up to 8 otherwise) it runs passes of
+ * ldda and 16-byte aligned X and dA; up to 12 otherwise) it runs passes of
  * its own kernel, each after the first continuing from the sums the
  * previous ones stored; from there on it runs ff_gemm (transa = 1 on dY),
  * which forms the same terms in the same order. */

@@ -381,7 +381,7 @@ __device__ __forceinline__ float2 add22_from_zero(float2 t, bool warp_fast)
     return ffk::add22(make_float2(0.0f, 0.0f), t);
 }
 
-// dA for k <= 8 with 16-byte access along the rows of dA: one thread per
+// dA for k <= 12 with 16-byte access along the rows of dA: one thread per
 // pair of adjacent columns, the thread's k column-pair values of X in
 // registers.  Block row y takes the rows [y rpb, (y + 1) rpb) (rpb even) in
 // pairs, so a thread forms 4 elements per step; the block stages the dY
@@ -390,7 +390,7 @@ __device__ __forceinline__ float2 add22_from_zero(float2 t, bool warp_fast)
 // Add22((0, 0), term_0), then Add22 of terms 1 .. k-1, in order (the first
 // step through add22_from_zero, bit-identical).  With ACC the elements
 // continue from the values dA holds (the partial sums of the right-hand
-// sides before these k: a second pass for 8 < k <= 16), adding terms 0 .. k-1
+// sides before these k: the later passes for 12 < k <= 16), adding terms 0 .. k-1
 // in order.  Lanes past the last column pair work on the last pair and do
 // not store, so that every lane of a warp takes part in the vote and every
 // thread reaches the block barriers.
@@ -496,12 +496,13 @@ gemv_dA_small_kernel(const float2* __restrict__ dY, int64_t m, int64_t lddy, con
     }
 }
 
-// Widest k that ff_gemv_dA runs on gemv_dA_small_kernel: one pass up to 8
-// right-hand sides, then passes that continue from the stored sums (loaded
-// one row pair ahead) up to 16; the GEMM kernel takes larger k (32768^2:
-// passes 0.92 against the GEMM route's 0.88-0.90 at k = 14-16, equal at
-// k = 20-24, 0.89-0.90 against 0.93-0.94 from k = 32).
-constexpr int kDAPass = 8;
+// Widest k that ff_gemv_dA runs on gemv_dA_small_kernel: one pass up to 12
+// right-hand sides (32768^2, k = 9-12: 0.93-0.95 of the FP32 roofline in one
+// pass against 0.87-0.89 in two), then passes of eight that continue from
+// the stored sums (loaded one row pair ahead) up to 16; the GEMM kernel
+// takes larger k (passes 0.90-0.92 against the GEMM route's 0.88-0.90 at
+// k = 13-16, equal at k = 20-24, 0.89-0.90 against 0.93-0.94 from k = 32).
+constexpr int kDAPass = 12;
 constexpr int kDAMaxSmallK = 16;
 
 template <bool ACC>
@@ -515,7 +516,11 @@ const void* dA_small_ptr(int k)
     case 5: return reinterpret_cast<const void*>(&gemv_dA_small_kernel<5, ACC>);
     case 6: return reinterpret_cast<const void*>(&gemv_dA_small_kernel<6, ACC>);
     case 7: return reinterpret_cast<const void*>(&gemv_dA_small_kernel<7, ACC>);
-    default: return reinterpret_cast<const void*>(&gemv_dA_small_kernel<8, ACC>);
+    case 8: return reinterpret_cast<const void*>(&gemv_dA_small_kernel<8, ACC>);
+    case 9: return reinterpret_cast<const void*>(&gemv_dA_small_kernel<9, ACC>);
+    case 10: return reinterpret_cast<const void*>(&gemv_dA_small_kernel<10, ACC>);
+    case 11: return reinterpret_cast<const void*>(&gemv_dA_small_kernel<11, ACC>);
+    default: return reinterpret_cast<const void*>(&gemv_dA_small_kernel<12, ACC>);
     }
 }
 
@@ -531,7 +536,11 @@ void launch_dA_small(int k, dim3 grid, cudaStream_t s, const float2* dY, int64_t
     case 5: gemv_dA_small_kernel<5, ACC><<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, dA, ldda, rpb); break;
     case 6: gemv_dA_small_kernel<6, ACC><<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, dA, ldda, rpb); break;
     case 7: gemv_dA_small_kernel<7, ACC><<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, dA, ldda, rpb); break;
-    default: gemv_dA_small_kernel<8, ACC><<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, dA, ldda, rpb); break;
+    case 8: gemv_dA_small_kernel<8, ACC><<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, dA, ldda, rpb); break;
+    case 9: gemv_dA_small_kernel<9, ACC><<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, dA, ldda, rpb); break;
+    case 10: gemv_dA_small_kernel<10, ACC><<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, dA, ldda, rpb); break;
+    case 11: gemv_dA_small_kernel<11, ACC><<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, dA, ldda, rpb); break;
+    default: gemv_dA_small_kernel<12, ACC><<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, dA, ldda, rpb); break;
     }
 }
 
@@ -729,14 +738,14 @@ ff_status ff_gemv_dA(const ff2* dY_, int64_t m, int64_t lddy, const ff2* X_, int
     const ff_status st = ffh::device_info(&di);
     if (st != FF_OK) return st;
     if (vec) {
-        // up to eight right-hand sides in one pass from (0, 0); more in
+        // up to kDAPass right-hand sides in one pass from (0, 0); more in
         // passes of the widths tile_for gives (eight, and nine to eleven
         // remaining as two halves), each continuing from the sums the
         // previous ones stored: a narrow pass is bound by re-reading dA
         // (32768^2: k = 9 as 8 + 1 measured 0.78 of the roofline, as 5 + 4
-        // 0.86; k = 12 as 8 + 4 0.89, as 6 + 6 0.87)
+        // 0.86)
         for (int64_t c0 = 0; c0 < k;) {
-            const int kt = tile_for(k - c0);
+            const int kt = (k - c0) <= kDAPass ? static_cast<int>(k - c0) : tile_for(k - c0);
             dim3 grid;
             int64_t rpb;
             if (c0 == 0) {
