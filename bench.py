@@ -991,15 +991,17 @@ def run_case(args):
     elif args.case in ("dot2", "sum2"):
         g = inputs.ill_dot_f32(n, 1e12, inputs.seed_for(5, 12), device=dev)
         fn = (lambda: ff.dot2(g.x, g.y)) if args.case == "dot2" else (lambda: ff.sum2(g.x))
-    elif args.case == "batch":
+    elif args.case in ("batch", "batch_packed"):
         # 256 dot / AXPY instances, lengths log-uniform over 1e2..1e6 (a small
-        # sample of the 4096-instance workload), one persistent launch
+        # sample of the 4096-instance workload), one persistent launch; with
+        # batch_packed the instances lie back to back (every instance after an
+        # odd length starts 8 bytes off a 16-byte boundary)
         from paper_cs_0603115_gb300 import batch
         lengths, kinds = inputs.batch_lengths(256, inputs.seed_for(3, 0), hi_exp=6.0)
         offs, o = [], 0
         for ln in lengths:
             offs.append(o)
-            o += ln + (ln & 1)
+            o += ln + (ln & 1 if args.case == "batch" else 0)
         gx = torch.Generator(device=dev).manual_seed(inputs.seed_for(3, 11))
         X = inputs.to_ff(inputs.loguniform_f64(o, gx, dev))
         Y = inputs.to_ff(inputs.loguniform_f64(o, gx, dev))
