@@ -16,6 +16,7 @@
 // accumulates its rows in order; the row blocks' partial sums go to the
 // workspace and a second kernel adds them in row-block order.
 #include "ff_core.cuh"
+#include "ff_first_term.cuh"
 #include "ff_host.cuh"
 
 namespace {
@@ -360,27 +361,6 @@ gemv_dA_scalar_kernel(const float2* __restrict__ dY, int64_t m, int64_t lddy, co
 // Rows per shared-memory chunk of dY in the weight-gradient kernel (even).
 constexpr int kTChunk = 128;
 
-// Add22((+0, +0), t) bit for bit, with two additions instead of the full
-// sequence when t is a finite pair whose sum rounds to its high part (every
-// Mul22 result is one: it ends with Add12).  For such t the Add22 theorem's
-// steps reduce to r = th (+) 0, s = tl (+) 0 and Add12(r, s) = (r, s):
-// th - r = +0 (the tie branch when th = +-0, which forces tl = +-0), the zero
-// operand's low part adds nothing, and Add12 of a pair whose sum rounds to its
-// first part returns the pair.  "(+) 0" does what the full sequence does to a
-// negative zero (it becomes +0).  Any other t (infinite, NaN, not normalised)
-// takes the full sequence.  The test is voted over the warp so that the
-// branch never diverges; every lane of the warp must be present.
-__device__ __forceinline__ bool from_zero_fast(float2 t)
-{
-    return fabsf(t.x) <= 3.40282347e38f && __fadd_rn(t.x, t.y) == t.x;
-}
-
-__device__ __forceinline__ float2 add22_from_zero(float2 t, bool warp_fast)
-{
-    if (warp_fast) return make_float2(__fadd_rn(t.x, 0.0f), __fadd_rn(t.y, 0.0f));
-    return ffk::add22(make_float2(0.0f, 0.0f), t);
-}
-
 // dA for k <= 12 with 16-byte access along the rows of dA: one thread per
 // pair of adjacent columns, the thread's k column-pair values of X in
 // registers.  Block row y takes the rows [y rpb, (y + 1) rpb) (rpb even) in
@@ -449,12 +429,13 @@ gemv_dA_small_kernel(const float2* __restrict__ dY, int64_t m, int64_t lddy, con
                 const float2 t01 = ffk::mul22(make_float2(d01.x, d01.y), xh[0]);
                 const float2 t10 = ffk::mul22(make_float2(d01.z, d01.w), xl[0]);
                 const float2 t11 = ffk::mul22(make_float2(d01.z, d01.w), xh[0]);
-                const bool fast = __all_sync(0xffffffffu, from_zero_fast(t00) && from_zero_fast(t01) &&
-                                                              from_zero_fast(t10) && from_zero_fast(t11));
-                a00 = add22_from_zero(t00, fast);
-                a01 = add22_from_zero(t01, fast);
-                a10 = add22_from_zero(t10, fast);
-                a11 = add22_from_zero(t11, fast);
+                const bool fast = __all_sync(0xffffffffu, ffk::from_zero_fast(t00) && ffk::from_zero_fast(t01) &&
+                                                              ffk::from_zero_fast(t10) &&
+                                                              ffk::from_zero_fast(t11));
+                a00 = ffk::add22_from_zero(t00, fast);
+                a01 = ffk::add22_from_zero(t01, fast);
+                a10 = ffk::add22_from_zero(t10, fast);
+                a11 = ffk::add22_from_zero(t11, fast);
             }
 #pragma unroll
             for (int c = C0; c < KT; ++c) {
@@ -482,9 +463,9 @@ gemv_dA_small_kernel(const float2* __restrict__ dY, int64_t m, int64_t lddy, con
         } else {
             const float2 d = __ldg(dY + r);
             const float2 t0 = ffk::mul22(d, xl[0]), t1 = ffk::mul22(d, xh[0]);
-            const bool fast = __all_sync(0xffffffffu, from_zero_fast(t0) && from_zero_fast(t1));
-            a0 = add22_from_zero(t0, fast);
-            a1 = add22_from_zero(t1, fast);
+            const bool fast = __all_sync(0xffffffffu, ffk::from_zero_fast(t0) && ffk::from_zero_fast(t1));
+            a0 = ffk::add22_from_zero(t0, fast);
+            a1 = ffk::add22_from_zero(t1, fast);
         }
 #pragma unroll
         for (int c = C0; c < KT; ++c) {
