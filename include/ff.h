@@ -398,7 +398,8 @@ FF_API ff_status ff_f64_add(const double* a, const double* b, double* out, size_
 FF_API ff_status ff_f64_mul(const double* a, const double* b, double* out, size_t n, cudaStream_t s);
 FF_API ff_status ff_f64_div(const double* a, const double* b, double* out, size_t n, cudaStream_t s);
 FF_API ff_status ff_f64_sqrt(const double* a, double* out, size_t n, cudaStream_t s);
-/* Binary64 dot product (fma accumulation, same tree shape as ff_dot). */
+/* Binary64 dot product (fma accumulation, same tree shape as ff_dot); ws as
+ * for ff_sum (a reduction workspace, its ticket zero). */
 FF_API ff_status ff_f64_dot(const double* x, const double* y, size_t n, double* out_dev, void* ws,
                      size_t ws_bytes, cudaStream_t s);
 /* Binary64 GEMV, same layouts as ff_gemv. */
