@@ -254,11 +254,11 @@ FF_API ff_status ff_gemv_t_launch_shape(const ff2* A, int64_t m, int64_t n, int6
  * it must not overlap dY or X.  1 <= k <= 64.  Every element starts from
  * (0, 0) as the sum's definition says; its first Add22 (with the zero) is
  * formed in two additions when the term is a finite normalised pair (the
- * same bits), the full Add22 otherwise.  Up to k = 16 (with even n, ldx and
- * ldda and 16-byte aligned X and dA; up to 12 otherwise) it runs passes of
- * its own kernel, each after the first continuing from the sums the
- * previous ones stored; from there on it runs ff_gemm (transa = 1 on dY),
- * which forms the same terms in the same order. */
+ * same bits), the full Add22 otherwise.  Up to k = 21 (with even n, ldx and
+ * ldda and 16-byte aligned X and dA; up to 12 otherwise) it runs its own
+ * kernel, in one pass up to k = 12 and in two above (the second continuing
+ * from the sums the first stored); from there on it runs ff_gemm
+ * (transa = 1 on dY), which forms the same terms in the same order. */
 FF_API ff_status ff_gemv_dA(const ff2* dY, int64_t m, int64_t lddy, const ff2* X, int64_t n, int64_t ldx,
                             int64_t k, ff2* dA, int64_t ldda, cudaStream_t s);
 

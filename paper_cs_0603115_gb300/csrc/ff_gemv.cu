@@ -340,10 +340,12 @@ int64_t row_blocks(int64_t m, int64_t n, int64_t k, bool vec, int sm_count)
 // ---------------------------------------------------------------------------
 // dA = dY X^T.  Every element accumulates its k terms Mul22(dY[r, c], X[j, c])
 // in order c = 0 .. k-1 from (0, 0), so the result is the oracle's
-// left-to-right sum bit for bit.  k > 4 runs as the matrix product
-// op(dY) X on the GEMM kernel (the same terms in the same order); k <= 4 runs
-// here: one thread per pair of adjacent columns (16-byte access) or per
-// column, rows walked by a grid of about one wave of blocks.
+// left-to-right sum bit for bit.  With 16-byte access along the rows of dA,
+// k <= 21 runs here in one or two passes (gemv_dA_small_kernel); without it,
+// k <= 12 runs here with one thread per column (gemv_dA_scalar_kernel).
+// Larger k runs as the matrix product op(dY) X on the GEMM kernel (the same
+// terms in the same order).  Both kernels walk the rows with a grid of about
+// one wave of blocks.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kGBlock)
 gemv_dA_scalar_kernel(const float2* __restrict__ dY, int64_t m, int64_t lddy, const float2* __restrict__ X,
@@ -361,7 +363,7 @@ gemv_dA_scalar_kernel(const float2* __restrict__ dY, int64_t m, int64_t lddy, co
 // Rows per shared-memory chunk of dY in the weight-gradient kernel (even).
 constexpr int kTChunk = 128;
 
-// dA for k <= 12 with 16-byte access along the rows of dA: one thread per
+// dA for up to 12 right-hand sides with 16-byte access along the rows of dA: one thread per
 // pair of adjacent columns, the thread's k column-pair values of X in
 // registers.  Block row y takes the rows [y rpb, (y + 1) rpb) (rpb even) in
 // pairs, so a thread forms 4 elements per step; the block stages the dY
@@ -370,12 +372,20 @@ constexpr int kTChunk = 128;
 // Add22((0, 0), term_0), then Add22 of terms 1 .. k-1, in order (the first
 // step through add22_from_zero, bit-identical).  With ACC the elements
 // continue from the values dA holds (the partial sums of the right-hand
-// sides before these k: the later passes for 12 < k <= 16), adding terms 0 .. k-1
-// in order.  Lanes past the last column pair work on the last pair and do
-// not store, so that every lane of a warp takes part in the vote and every
-// thread reaches the block barriers.
+// sides before these k: the second pass for 12 < k <= 21), adding terms
+// 0 .. k-1 in order.  Lanes past the last column pair work on the last pair
+// and do not store, so that every lane of a warp takes part in the vote and
+// every thread reaches the block barriers.
+//
+// Resident blocks per SM the register allocation must leave room for: a
+// continuing pass of ten or more right-hand sides took 98-100 registers on
+// its own (two blocks per SM) and ran at 0.82-0.83 of the FP32 roofline
+// (32768^2, k = 18-20 as 8 + 10 .. 8 + 12); at 80 registers (three blocks)
+// k = 20 as 10 + 10 runs at 0.92.
+constexpr int dA_min_blocks(int kt, bool acc) { return acc && kt >= 10 ? 3 : 0; }
+
 template <int KT, bool ACC>
-__global__ void __launch_bounds__(kGBlock)
+__global__ void __launch_bounds__(kGBlock, dA_min_blocks(KT, ACC))
 gemv_dA_small_kernel(const float2* __restrict__ dY, int64_t m, int64_t lddy, const float2* __restrict__ X, int64_t n,
                      int64_t ldx, float2* __restrict__ dA, int64_t ldda, int64_t rpb)
 {
@@ -479,12 +489,20 @@ gemv_dA_small_kernel(const float2* __restrict__ dY, int64_t m, int64_t lddy, con
 
 // Widest k that ff_gemv_dA runs on gemv_dA_small_kernel: one pass up to 12
 // right-hand sides (32768^2, k = 9-12: 0.93-0.95 of the FP32 roofline in one
-// pass against 0.87-0.89 in two), then passes of eight that continue from
-// the stored sums (loaded one row pair ahead) up to 16; the GEMM kernel
-// takes larger k (passes 0.90-0.92 against the GEMM route's 0.88-0.90 at
-// k = 13-16, equal at k = 20-24, 0.89-0.90 against 0.93-0.94 from k = 32).
+// pass against 0.87-0.89 in two), then two passes of ceil(k/2) and floor(k/2),
+// the second continuing from the stored sums (loaded one row pair ahead), up
+// to 21; the GEMM kernel takes larger k.  32768^2, fractions of the FP32
+// roofline, two passes against the GEMM route: k = 13-21 0.90-0.92 against
+// 0.87-0.90; k = 22-23 0.89-0.90 against 0.90; k = 24 (12 + 12, where the
+// continuing pass spills at 80 registers) 0.85 against 0.91.
 constexpr int kDAPass = 12;
-constexpr int kDAMaxSmallK = 16;
+constexpr int kDAMaxSmallK = 21;
+// The continuing pass is the second of two and takes floor(k/2) <= 10
+// right-hand sides: no wider continuing kernel is compiled (dA_kt maps the
+// cases above ten of the switches below to it; the pass loop never takes
+// them).
+constexpr int kDAMaxAccKT = kDAMaxSmallK / 2;
+constexpr int dA_kt(int kt, bool acc) { return acc && kt > kDAMaxAccKT ? kDAMaxAccKT : kt; }
 
 template <bool ACC>
 const void* dA_small_ptr(int k)
@@ -500,8 +518,8 @@ const void* dA_small_ptr(int k)
     case 8: return reinterpret_cast<const void*>(&gemv_dA_small_kernel<8, ACC>);
     case 9: return reinterpret_cast<const void*>(&gemv_dA_small_kernel<9, ACC>);
     case 10: return reinterpret_cast<const void*>(&gemv_dA_small_kernel<10, ACC>);
-    case 11: return reinterpret_cast<const void*>(&gemv_dA_small_kernel<11, ACC>);
-    default: return reinterpret_cast<const void*>(&gemv_dA_small_kernel<12, ACC>);
+    case 11: return reinterpret_cast<const void*>(&gemv_dA_small_kernel<dA_kt(11, ACC), ACC>);
+    default: return reinterpret_cast<const void*>(&gemv_dA_small_kernel<dA_kt(12, ACC), ACC>);
     }
 }
 
@@ -520,8 +538,12 @@ void launch_dA_small(int k, dim3 grid, cudaStream_t s, const float2* dY, int64_t
     case 8: gemv_dA_small_kernel<8, ACC><<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, dA, ldda, rpb); break;
     case 9: gemv_dA_small_kernel<9, ACC><<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, dA, ldda, rpb); break;
     case 10: gemv_dA_small_kernel<10, ACC><<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, dA, ldda, rpb); break;
-    case 11: gemv_dA_small_kernel<11, ACC><<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, dA, ldda, rpb); break;
-    default: gemv_dA_small_kernel<12, ACC><<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, dA, ldda, rpb); break;
+    case 11:
+        gemv_dA_small_kernel<dA_kt(11, ACC), ACC><<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, dA, ldda, rpb);
+        break;
+    default:
+        gemv_dA_small_kernel<dA_kt(12, ACC), ACC><<<grid, kGBlock, 0, s>>>(dY, m, lddy, X, n, ldx, dA, ldda, rpb);
+        break;
     }
 }
 
@@ -720,13 +742,13 @@ ff_status ff_gemv_dA(const ff2* dY_, int64_t m, int64_t lddy, const ff2* X_, int
     if (st != FF_OK) return st;
     if (vec) {
         // up to kDAPass right-hand sides in one pass from (0, 0); more in
-        // passes of the widths tile_for gives (eight, and nine to eleven
-        // remaining as two halves), each continuing from the sums the
-        // previous ones stored: a narrow pass is bound by re-reading dA
+        // two passes of ceil(k/2) and floor(k/2), the second continuing from
+        // the sums the first stored: a narrow pass is bound by re-reading dA
         // (32768^2: k = 9 as 8 + 1 measured 0.78 of the roofline, as 5 + 4
-        // 0.86)
+        // 0.86; k = 13 as 12 + 1 0.81, as 7 + 6 0.92)
         for (int64_t c0 = 0; c0 < k;) {
-            const int kt = (k - c0) <= kDAPass ? static_cast<int>(k - c0) : tile_for(k - c0);
+            const int64_t rest = k - c0;
+            const int kt = static_cast<int>(rest <= kDAPass ? rest : (rest + 1) / 2);
             dim3 grid;
             int64_t rpb;
             if (c0 == 0) {

@@ -490,14 +490,16 @@ def test_gemv_result_does_not_depend_on_k(n):
                                    (300, 998, 2), (257, 66, 7), (256, 514, 8), (1000, 2050, 5), (999, 130, 6),
                                    (40, 20, 9), (301, 130, 12), (256, 66, 16), (33, 64, 15), (17, 129, 12),
                                    (70, 50, 17), (100, 130, 13), (99, 64, 10), (129, 66, 11), (5, 2, 3),
-                                   (1, 4, 12), (2, 2, 1)])
+                                   (1, 4, 12), (2, 2, 1), (66, 64, 21), (35, 130, 19), (41, 32, 20),
+                                   (7, 2, 13), (130, 66, 22), (33, 65, 19)])
 def test_gemv_dA_bitexact(m, n, k):
     gi = inputs.gemv(m, n, k, inputs.seed_for(4, 50 + k))
     dA = ff.gemv_dA(gpu(gi.dY), gpu(gi.X)).cpu().numpy()
     same_bits(dA, oracle.gemv_dA(gi.dY.numpy(), gi.X.numpy()))
 
 
-@pytest.mark.parametrize("m,n,k", [(130, 66, 1), (129, 128, 2), (64, 70, 3), (66, 64, 8), (65, 66, 12)])
+@pytest.mark.parametrize("m,n,k", [(130, 66, 1), (129, 128, 2), (64, 70, 3), (66, 64, 8), (65, 66, 12),
+                                   (65, 66, 20)])
 def test_gemv_dA_special_values_bitexact(m, n, k):
     """dA's first term takes a shortcut for finite normalised products and
     the full Add22 from (0, 0) otherwise: signed zeros, subnormals,
