@@ -1,6 +1,7 @@
-// ff_gemv.cu -- float-float GEMV Y = A X and its adjoint dX = A^T dY, each
-// term a Mul22 and each accumulation an Add22 (the paper's operators), plus a
-// binary64 GEMV baseline with the same layouts.
+// ff_gemv.cu -- float-float GEMV Y = A X, its adjoint dX = A^T dY and the
+// weight gradient dA = dY X^T, each term a Mul22 and each accumulation an
+// Add22 (the paper's operators), plus a binary64 GEMV baseline with the same
+// layouts.
 //
 // Layouts: A is m x n row-major (row stride lda); X, dX are n x k and Y, dY
 // are m x k, all column-major (column strides ldx, lddx, ldy, lddy).
@@ -15,6 +16,11 @@
 // 16-byte loads along rows), one block row per row block of A.  Each thread
 // accumulates its rows in order; the row blocks' partial sums go to the
 // workspace and a second kernel adds them in row-block order.
+//
+// ff_gemv_dA: one thread per pair of adjacent columns of dA, the block's
+// rows walked in pairs with dY staged in shared memory; every element adds
+// its k terms in order from (0, 0), in one pass up to twelve right-hand
+// sides and two above, or through the GEMM kernel for larger k.
 #include "ff_core.cuh"
 #include "ff_first_term.cuh"
 #include "ff_host.cuh"
@@ -156,9 +162,9 @@ inline int f64_tile_for(int64_t k) { return k >= 16 ? 16 : k >= 8 ? 8 : k >= 4 ?
 // ---------------------------------------------------------------------------
 // dX = A^T dY
 // ---------------------------------------------------------------------------
-// Rows of A each thread of the adjoint loads before using them, for tiles
-// of up to seven right-hand sides: the fewer terms a row gives, the more
-// rows must be in flight to cover the HBM latency.
+// Rows of A each thread of the adjoint loads before using them (the tiles
+// are at most eight wide): the fewer terms a row gives, the more rows must
+// be in flight to cover the HBM latency.
 constexpr int kTRows(int kt) { return kt <= 2 ? 8 : 4; }
 
 // Resident blocks per SM the register allocation must leave room for: with
