@@ -189,7 +189,8 @@ FF_API ff_status ff_dot_backward(const ff2* dout_dev, const ff2* x, const ff2* y
 /* Compensated sum and dot product of plain binary32 vectors (the paper's
  * compensated algorithms, future work in Section 7): Ogita, Rump and Oishi's Sum2 and
  * Dot2 (2005) with Add12 as TwoSum and the fused Mul12 as TwoProduct, per
- * thread in the sweep order of ff_sum, combined across threads, warps and
+ * thread in the sweep order of ff_sum (16-byte chunks of four values, up to
+ * three leading values alone on thread 0), combined across threads, warps and
  * blocks by (p, q) = TwoSum(a.p, b.p), s = a.s + (b.s + q).  *out_dev is the
  * float-float Add12(p, s).  x, y: 4-byte aligned binary32 arrays; ws as for
  * ff_sum.  Reads 4 (Sum2) or 8 (Dot2) bytes per value, half of ff_sum /

@@ -6,10 +6,13 @@
 // One launch per reduction.  Order of combination (fixed for a given n,
 // device and build, hence bit-reproducible):
 //   1. thread t of T = grid x 256 threads starts from zero and accumulates,
-//      left to right, the head element (thread 0 only, when the arrays are
-//      not 16-byte aligned), then the two-element chunks t, t + T, t + 2T, ...
-//      (element pair 2c, 2c+1 of chunk c, in that order), then the odd tail
-//      element (thread 0 only);
+//      left to right, the head elements before the first 16-byte boundary
+//      (thread 0 only; none when the arrays are 16-byte aligned), then the
+//      16-byte chunks t, t + T, t + 2T, ... (E = 2 float-float or binary64
+//      values, 4 binary32 values; the values of chunk c in increasing
+//      order), then the tail elements after the last whole chunk (thread 0
+//      only).  Arrays whose offsets modulo 16 bytes differ take one element
+//      per step instead: elements t, t + T, t + 2T, ...;
 //   2. each warp combines lanes with a shuffle-down tree
 //      (v_l = combine(v_l, v_{l+off}), off = 16, 8, 4, 2, 1);
 //   3. lane 0 of each warp stores its value; warp 0 combines the 8 warp
