@@ -8,11 +8,18 @@ C ABI in ``libff.so`` (include/ff.h) on the current CUDA stream; all
 arithmetic runs in the library's CUDA kernels.  Nothing falls back to the CPU:
 a missing library or a non-CUDA tensor raises.
 
-Elementwise:  add12, mul12 (packed (a, b) pairs), add, mul, div, sqrt, axpy
-Reductions:   sum, dot (device-resident float-float result), dot_backward
-GEMV:         gemv (Y = A X), gemv_t (dX = A^T dY)
-Autograd:     FFDot, FFGemv (hand-written adjoint kernels)
-Baselines:    f64_add/mul/div/sqrt/dot/gemv, f32_add/mul/mad
+Elementwise:  add12, mul12 (packed (a, b) pairs), add, add_accurate, mul, div,
+              sqrt, axpy
+Reductions:   sum, dot (device-resident float-float result), sum2, dot2
+              (binary32 inputs), dot_backward
+GEMV, GEMM:   gemv (Y = A X), gemv_t (dX = A^T dY), gemv_dA (dA = dY X^T),
+              gemm (C = op(A) op(B))
+Autograd:     FFDot, FFGemv, FFGemm and ffdot, ffgemv, ffgemm (hand-written
+              adjoint kernels)
+Baselines:    f64_add/mul/div/sqrt/dot/gemv, f32_add/mul/mad, fma_peak
+Submodules:   batch (many instances in one persistent launch, CUDA graphs,
+              autotuner), dist (sharded reductions over processes), inputs
+              (the seeded input recipe)
 """
 from __future__ import annotations
 

@@ -1,4 +1,5 @@
-"""Batched float-float dot / AXPY instances in one persistent launch.
+"""Batched float-float dot, AXPY, dot-adjoint and GEMV instances in one
+persistent launch.
 
 Thin wrapper over the C ABI's ff_batch_* entry points: a ``BatchPlan`` holds
 the native plan (instance records and tile list on the device), its
