@@ -53,6 +53,12 @@ MUTANTS = [
     ("fast2sum: sign", "    float t = b - z;", "    float t = z - b;"),
     ("sum2: error term dropped", "        add12(p, x[i], &p, &q);\n        s = s + q;", "        add12(p, x[i], &p, &q);\n        s = s + 0.0f * q;"),
     ("dot2: product error r dropped", "        s = s + (q + r);", "        s = s + q;"),
+    ("gemv_dA: X of the first right-hand side for every term",
+     "const float *dy = &dY[2 * (c * lddy + r)];\n                const float *xv = &X[2 * (c * ldx + j)];",
+     "const float *dy = &dY[2 * (c * lddy + r)];\n                const float *xv = &X[2 * j];"),
+    ("gemv_dA: dY of row 0 for every row",
+     "const float *dy = &dY[2 * (c * lddy + r)];\n                const float *xv = &X[2 * (c * ldx + j)];",
+     "const float *dy = &dY[2 * (c * lddy)];\n                const float *xv = &X[2 * (c * ldx + j)];"),
     ("gemm: op(A) index not transposed", "transa ? &A[2 * (p * lda + i)]", "transa ? &A[2 * (i * lda + p)]"),
     ("gemm: B read by column", ": &B[2 * (p * ldb + j)];", ": &B[2 * (j * ldb + p)];"),
 ]
