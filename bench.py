@@ -509,8 +509,11 @@ def extra_rows(torch, ff, inputs, e, dev, peaks):
     red_out = torch.empty(2, dtype=torch.float32, device=dev)
 
     def red_row(fn, nbytes, nops, key):
+        # device time per call from a CUDA graph of 20 calls; and the same
+        # calls issued one by one from Python, 50 of them, so that the host's
+        # time to issue the first call is spread over many
         t = graph_time(torch, fn, 20)
-        tl = time_fn(torch, fn, 10)
+        tl = time_fn(torch, fn, 50)
         return {"ms": round(t * 1e3, 4), "loop_ms": round(tl * 1e3, 4), "GB/s": round(nbytes / t / 1e9, 1),
                 "frac_hbm": round(nbytes / t / 1e9 / hbm, 4), "frac_hbm_loop": round(nbytes / tl / 1e9 / hbm, 4),
                 key: nops / t}
