@@ -46,9 +46,9 @@
 #include "ff_core.cuh"
 #include "ff_host.cuh"
 
-// Internal record kind: rows of a GEMV instance, one warp per row.
+// Internal record kind: rows of a GEMV instance, eight lanes per row.
 constexpr int32_t kGemvRows = 100;
-// GEMV rows up to this length are reduced by one warp each; longer rows
+// GEMV rows up to this length are reduced by eight lanes each; longer rows
 // become dot records reduced by whole blocks over several tiles.
 constexpr int64_t kWarpRowMax = 65536;
 
