@@ -509,6 +509,8 @@ constexpr int kDAMaxSmallK = 21;
 // them).
 constexpr int kDAMaxAccKT = kDAMaxSmallK / 2;
 constexpr int dA_kt(int kt, bool acc) { return acc && kt > kDAMaxAccKT ? kDAMaxAccKT : kt; }
+static_assert((kDAMaxSmallK + 1) / 2 <= kDAPass && kDAMaxSmallK <= 2 * kDAPass,
+              "beyond one pass, ff_gemv_dA runs exactly two passes of at most kDAPass right-hand sides");
 
 template <bool ACC>
 const void* dA_small_ptr(int k)
