@@ -477,7 +477,7 @@ def test_gemv_t_bitexact_vs_order_replay(m, n, k):
 @pytest.mark.parametrize("n", [1000, 999])
 def test_gemv_result_does_not_depend_on_k(n):
     """Every right-hand side is reduced in the same order whatever k and the
-    tile widths are: k = 20 in one call (tiles 16 + 4) equals 20 one-column
+    tile widths are: k = 20 in one call (tiles 8 + 8 + 4) equals 20 one-column
     calls bit for bit, with 16-byte access (n even) and without (n odd)."""
     gi = inputs.gemv(300, n, 20, inputs.seed_for(4, 95 + n % 2))
     A, X = gpu(gi.A), gpu(gi.X)
