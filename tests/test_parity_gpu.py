@@ -520,6 +520,27 @@ def test_gemv_dA_special_values_bitexact(m, n, k):
     same_bits(dA, oracle.gemv_dA(dY, X))
 
 
+def test_gemv_family_empty_sums_and_empty_outputs():
+    """Degenerate sizes: with n = 0 every element of Y = A X is an empty sum,
+    (+0, +0), and so is every element of dX = A^T dY with m = 0; outputs
+    with no elements (m = 0 for Y and dA, n = 0 for dA) are returned empty
+    and nothing is written."""
+    Y = torch.full((3, 5, 2), 7.25, device=DEV)
+    ff.gemv(torch.empty((5, 0, 2), device=DEV), torch.empty((3, 0, 2), device=DEV), out=Y)
+    dX = torch.full((3, 6, 2), 7.25, device=DEV)
+    ff.gemv_t(torch.empty((0, 6, 2), device=DEV), torch.empty((3, 0, 2), device=DEV), out=dX)
+    torch.cuda.synchronize()
+    assert torch.count_nonzero(Y.view(torch.int32)) == 0
+    assert torch.count_nonzero(dX.view(torch.int32)) == 0
+    gi = inputs.gemv(5, 6, 3, inputs.seed_for(4, 170))
+    A, X, dY = gpu(gi.A), gpu(gi.X), gpu(gi.dY)
+    assert ff.gemv(A[:0].contiguous(), X).shape == (3, 0, 2)
+    assert ff.gemv_t(A[:, :0].contiguous(), dY).shape == (3, 0, 2)
+    assert ff.gemv_dA(dY[:, :0].contiguous(), X).shape == (0, 6, 2)
+    assert ff.gemv_dA(dY, X[:, :0].contiguous()).shape == (5, 0, 2)
+    torch.cuda.synchronize()
+
+
 def test_gemv_autograd_weight_gradient():
     gi = inputs.gemv(48, 80, 3, inputs.seed_for(4, 60))
     A = gpu(gi.A).requires_grad_(True)
