@@ -115,6 +115,28 @@ def test_batch_with_dot_gradients(tune):
     plan.close()
 
 
+@pytest.mark.parametrize("tune", [None, (128, 16, 0)])
+def test_batch_thousands_of_small_instances(tune):
+    """3000 instances of 0 to 300 values, dot, AXPY and dot-gradient in
+    turn: most are single-tile records and a block walks many of them.
+    Every AXPY and gradient value bit for bit, every dot within its bound,
+    on two runs (the second on the counters the first left at zero)."""
+    from paper_cs_0603115_gb300 import batch
+    rng = np.random.default_rng(77)
+    lengths = [int(v) for v in rng.integers(0, 301, 3000)]
+    kinds = [(batch.DOT, batch.AXPY, batch.DOT_GRAD)[i % 3] for i in range(len(lengths))]
+    specs, keep = build_case(lengths, kinds, 9000)
+    plan = batch.BatchPlan(batch.make_instances(specs), tune=tune)
+    for _ in range(2):
+        for _, _, _, _, out in keep:
+            for t in (out if isinstance(out, tuple) else (out,)):
+                t.fill_(float("nan"))
+        plan.run()
+        torch.cuda.synchronize()
+        check(keep)
+    plan.close()
+
+
 def test_batch_graph_and_plain_agree():
     import paper_cs_0603115_gb300 as ff
     from paper_cs_0603115_gb300 import batch
