@@ -491,7 +491,7 @@ def test_gemv_result_does_not_depend_on_k(n):
                                    (40, 20, 9), (301, 130, 12), (256, 66, 16), (33, 64, 15), (17, 129, 12),
                                    (70, 50, 17), (100, 130, 13), (99, 64, 10), (129, 66, 11), (5, 2, 3),
                                    (1, 4, 12), (2, 2, 1), (66, 64, 21), (35, 130, 19), (41, 32, 20),
-                                   (7, 2, 13), (130, 66, 22), (33, 65, 19)])
+                                   (7, 2, 13), (130, 66, 22), (33, 65, 19), (5001, 4, 17), (3, 5000, 20)])
 def test_gemv_dA_bitexact(m, n, k):
     gi = inputs.gemv(m, n, k, inputs.seed_for(4, 50 + k))
     dA = ff.gemv_dA(gpu(gi.dY), gpu(gi.X)).cpu().numpy()
