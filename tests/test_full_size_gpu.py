@@ -1,0 +1,130 @@
+"""Parity at the benchmark's full sizes, in the launch configuration bench.py
+times, on outputs the oracle can check one by one: the batched workload of
+4096 dot and AXPY instances (3.7e9 values, the autotuner's launch shape) and
+the GEMV family on the 32768 x 32768 matrix.  The elementwise operators and
+the reductions at full size are covered in test_parity_gpu.py and
+test_compensated_gpu.py, the 4096^3 GEMM in test_gemm_gpu.py."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_cs_0603115_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda"
+
+if torch.cuda.is_available():
+    import paper_cs_0603115_gb300 as ff
+
+
+def same_bits(got, want):
+    got = np.ascontiguousarray(got, np.float32)
+    want = np.ascontiguousarray(want, np.float32)
+    assert got.shape == want.shape
+    nan = np.isnan(got) & np.isnan(want)
+    assert ((got.view(np.uint32) == want.view(np.uint32)) | nan).all()
+
+
+def _sample(idx, count, rng):
+    """`count` indices of `idx` (a list ordered by length), always with the
+    shortest and the longest."""
+    pick = set(rng.choice(len(idx), size=min(count, len(idx)) - 2, replace=False).tolist()) | {0, len(idx) - 1}
+    return [idx[p] for p in sorted(pick)]
+
+
+def test_batched_4096_instances_full_size_sampled():
+    """bench.py's batched workload (4096 instances, lengths log-uniform over
+    1e2..1e7, dots at cond 1e8 and AXPY with 10% cancelling pairs, every
+    instance at a 16-byte boundary) run once with the launch shape the
+    autotuner picks: 24 sampled AXPY instances bit for bit against the
+    oracle; 24 sampled dots within n 2^-46 sum |x_i y_i| of the exact value
+    and, up to 2e5 values, bit for bit against the replay of the batched
+    tile, thread and block order."""
+    import replay
+    from paper_cs_0603115_gb300 import batch
+    lengths, kinds = inputs.batch_lengths(4096, inputs.seed_for(3, 0))
+    offs, o = [], 0
+    for n in lengths:
+        offs.append(o)
+        o += n + (n & 1)
+    X = torch.empty((o, 2), dtype=torch.float32, device=DEV)
+    Y = torch.empty((o, 2), dtype=torch.float32, device=DEV)
+    Z = torch.full((o, 2), float("nan"), dtype=torch.float32, device=DEV)
+    D = torch.full((4096, 2), float("nan"), dtype=torch.float32, device=DEV)
+    alphas = [tuple(float(v) for v in inputs.scalar_ff(inputs.seed_for(3, 3) + i)) for i in range(4096)]
+    sl = [slice(offs[i], offs[i] + lengths[i]) for i in range(4096)]
+    for i, (n, kind) in enumerate(zip(lengths, kinds)):
+        if kind == batch.DOT:
+            g = inputs.ill_dot(n, 1e8, inputs.seed_for(3, 1) + 7 * i, device=DEV)
+            X[sl[i]].copy_(g.x)
+            Y[sl[i]].copy_(g.y)
+        else:
+            e = inputs.elementwise(n, inputs.seed_for(3, 2) + 7 * i, device=DEV)
+            X[sl[i]].copy_(e.a)
+            Y[sl[i]].copy_(e.b)
+    specs = [(k, X[sl[i]], Y[sl[i]], D[i] if k == batch.DOT else Z[sl[i]], alphas[i]) for i, k in enumerate(kinds)]
+    inst = batch.make_instances(specs)
+    tune, _ = batch.autotune(inst, reps=1, cache_path=None)
+    for t in (Z, D):
+        t.fill_(float("nan"))   # the autotuner's runs wrote them
+    plan = batch.BatchPlan(inst, tune=tune)
+    plan.run()
+    torch.cuda.synchronize()
+    block, ppt = plan.tune[0], plan.tune[1]
+    rng = np.random.default_rng(11)
+    by_len = sorted(range(4096), key=lambda i: lengths[i])
+    for i in _sample([j for j in by_len if kinds[j] == batch.AXPY], 24, rng):
+        x, y = X[sl[i]].cpu().numpy(), Y[sl[i]].cpu().numpy()
+        same_bits(Z[sl[i]].cpu().numpy(), oracle.axpy(np.array(alphas[i], np.float32), x, y))
+    for i in _sample([j for j in by_len if kinds[j] == batch.DOT], 24, rng):
+        x, y = X[sl[i]].cpu().numpy(), Y[sl[i]].cpu().numpy()
+        got = D[i].cpu().numpy()
+        _, _, a_abs, err = oracle.exact_dot(x, y, got)
+        assert abs(err) <= lengths[i] * 2.0 ** -46 * a_abs
+        if lengths[i] <= 200000:
+            same_bits(got, replay.batch_dot_replay(x, y, block, ppt, 1))
+    plan.close()
+    del X, Y, Z, D
+    torch.cuda.empty_cache()
+
+
+def test_gemv_family_full_size_sampled():
+    """The 32768 x 32768 matrix (8 GiB) of bench.py's GEMV sweep: with k = 3,
+    Y = A X on 16 sampled rows and dX = A^T dY on 16 sampled columns bit for
+    bit against the replays of their orders (the adjoint's row blocks read
+    from ff_gemv_t_launch_shape at this size); the weight gradient
+    dA = dY X^T with k = 3 (one pass) and k = 20 (two passes) on a 16 x 16
+    sample of elements bit for bit against the oracle."""
+    import replay
+    from paper_cs_0603115_gb300 import _lib
+    M = N = 32768
+    gi = inputs.gemv(M, N, 20, inputs.seed_for(4, 180), device=DEV)
+    A = gi.A
+    rng = np.random.default_rng(12)
+    rows = sorted(set(rng.choice(M, 14, replace=False).tolist()) | {0, M - 1})
+    cols = sorted(set(rng.choice(N, 14, replace=False).tolist()) | {0, N - 1})
+    X3, dY3 = gi.X[:3].contiguous(), gi.dY[:3].contiguous()
+    Y = ff.gemv(A, X3)
+    dX = ff.gemv_t(A, dY3)
+    torch.cuda.synchronize()
+    same_bits(Y[:, rows].cpu().numpy(), replay.gemv_warp_replay(A[rows].cpu().numpy(), X3.cpu().numpy(), vec=True))
+    nrb, vec = ctypes.c_int64(), ctypes.c_int()
+    _lib.call("ff_gemv_t_launch_shape", A.data_ptr(), M, N, N, 3, ctypes.byref(nrb), ctypes.byref(vec))
+    assert vec.value == 1
+    same_bits(dX[:, cols].cpu().numpy(),
+              replay.gemv_t_replay(A[:, cols].cpu().numpy(), dY3.cpu().numpy(), nrb.value))
+    del Y, dX
+    dA = torch.empty_like(A)
+    Xc, dYr = gi.X[:, cols].cpu().numpy(), gi.dY[:, rows].cpu().numpy()
+    for k in (3, 20):
+        dA.fill_(float("nan"))
+        ff.gemv_dA(gi.dY[:k].contiguous(), gi.X[:k].contiguous(), out=dA)
+        torch.cuda.synchronize()
+        got = dA[rows][:, cols].cpu().numpy()
+        same_bits(got, oracle.gemv_dA(np.ascontiguousarray(dYr[:k]), np.ascontiguousarray(Xc[:k])))
+    del dA, gi, A
+    torch.cuda.empty_cache()
