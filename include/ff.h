@@ -12,7 +12,8 @@
  *   - Memory.  Every array argument is a DEVICE pointer owned by the caller,
  *     at least 8-byte aligned (the alignment of ff2); 16-byte alignment is
  *     not required.  The library never allocates device memory inside a
- *     call: scratch space is a caller-owned workspace whose size the matching
+ *     call (ff_batch_plan_create, which builds a plan, is the one exception):
+ *     scratch space is a caller-owned workspace whose size the matching
  *     *_workspace_bytes() function returns.
  *   - Streams.  Calls only enqueue work on the caller's stream `s` (0 = the
  *     legacy default stream) and return at once; results, including the
@@ -25,7 +26,10 @@
  *     FF_ERR_INVALID_ARG; a workspace that is NULL or too small returns
  *     FF_ERR_WORKSPACE.  A failed launch returns FF_ERR_CUDA and keeps the
  *     CUDA error code for ff_last_cuda_error().  Nothing is enqueued when a
- *     call returns an error.
+ *     call returns an argument or workspace error; when a call that makes
+ *     several launches (a GEMV of several column tiles, a weight gradient
+ *     in two passes, a GEMV adjoint and its combination) fails to launch
+ *     one, the launches before it stay enqueued.
  *   - Sizes.  n == 0 is a no-op returning FF_OK, except that a reduction
  *     with n == 0 writes (0, 0) to its result.
  *   - Aliasing.  An elementwise output may be exactly one of its inputs
