@@ -426,9 +426,10 @@ FF_API ff_status ff_f32_mad(const float* a, const float* b, const float* c, floa
  * that the FP32-issue-bound kernels and the FP64 baselines are compared
  * with).  Launches `blocks` x `threads` threads; each runs eight independent
  * chains x <- fma(x, 1, 1) (binary32 when f64 == 0, binary64 when f64 == 1)
- * for `iters` rounds and writes the sum of its chains, x_0 + ... + x_7 +
- * 8 iters with x_c starting at c, to out[thread] (a device array of
- * blocks * threads floats or doubles, 8-byte aligned, owned by the caller).
+ * for `iters` rounds and writes the sum of its chains to out[thread] (a
+ * device array of blocks * threads floats or doubles, 8-byte aligned, owned
+ * by the caller); chain c starts at c and ends at c + iters, so every
+ * thread writes 28 + 8 iters.
  * One launch performs 16 * iters * blocks * threads floating-point
  * operations; the caller times it (CUDA events on `s`).  Invalid arguments
  * (f64 not 0/1, iters < 0, blocks < 1, threads not a multiple of 32 in
