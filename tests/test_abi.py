@@ -88,3 +88,50 @@ def test_product_never_imports_the_oracle():
     # the C sources of the oracle and the CUDA library share no file
     csrc = set(os.listdir(os.path.join(pkg, "csrc")))
     assert not (csrc & set(os.listdir(os.path.join(ROOT, "oracle"))))
+
+
+def _header_prototypes():
+    """(name -> (return type, [parameter types])) of every FF_API function in
+    include/ff.h, comments removed, parameter names dropped."""
+    from paper_cs_0603115_gb300 import _lib
+    text = open(_lib.HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    protos = {}
+    for ret, name, params in re.findall(r"FF_API\s+([\w\s\*]+?)\s*\b(ff_\w+)\s*\(([^)]*)\)\s*;", text):
+        types = []
+        for p in params.split(","):
+            p = " ".join(p.split())
+            if not p or p == "void":
+                continue
+            types.append(re.sub(r"\s*\b\w+$", "", p) if not p.endswith("*") else p)
+        protos[name] = (" ".join(ret.split()), types)
+    return protos
+
+
+def _ctypes_kind(t):
+    """A coarse class of a C parameter or return type for the comparison."""
+    t = t.replace("const ", "").strip()
+    if t.endswith("*") or t in ("cudaStream_t", "ff_batch_plan", "ff_batch_graph"):
+        return "pointer"
+    return {"size_t": "size", "int64_t": "int64", "int": "int", "ff_status": "int", "ff2": "ff2",
+            "void": "void"}[t]
+
+
+def test_binding_signatures_match_the_header():
+    """Every entry point's ctypes signature has the header's parameter count
+    and, parameter by parameter, the same kind of type (pointer, size_t,
+    int64_t, int, ff2 by value), and the same kind of return value: a
+    mismatched width would pass wrong values through the ABI silently."""
+    from paper_cs_0603115_gb300 import _lib
+    protos = _header_prototypes()
+    assert set(protos) == set(_lib.SIGNATURES), set(protos) ^ set(_lib.SIGNATURES)
+    py_kind = {ctypes.c_void_p: "pointer", ctypes.c_size_t: "size", ctypes.c_int64: "int64",
+               ctypes.c_int: "int", _lib.ff2: "ff2", ctypes.c_char_p: "pointer", None: "void"}
+    for name, (ret, params) in protos.items():
+        res, args = _lib.SIGNATURES[name]
+        assert len(args) == len(params), (name, params)
+        got = [py_kind.get(a, "pointer" if hasattr(a, "contents") or a.__name__.startswith("LP_") else "?")
+               for a in args]
+        want = [_ctypes_kind(p) for p in params]
+        assert got == want, (name, got, want)
+        assert py_kind[res] == _ctypes_kind(ret), (name, res, ret)
