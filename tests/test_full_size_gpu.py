@@ -1,9 +1,10 @@
 """Parity at the benchmark's full sizes, in the launch configuration bench.py
 times, on outputs the oracle can check one by one: the batched workload of
 4096 dot and AXPY instances (3.7e9 values, the autotuner's launch shape) and
-the GEMV family on the 32768 x 32768 matrix.  The elementwise operators and
-the reductions at full size are covered in test_parity_gpu.py and
-test_compensated_gpu.py, the 4096^3 GEMM in test_gemm_gpu.py."""
+the GEMV family on the 32768 x 32768 matrix, and the adjoint of the 2^26-value
+dot.  The elementwise operators and the reductions at full size are covered
+in test_parity_gpu.py and test_compensated_gpu.py, the 4096^3 GEMM in
+test_gemm_gpu.py."""
 import ctypes
 
 import numpy as np
@@ -127,4 +128,43 @@ def test_gemv_family_full_size_sampled():
         got = dA[rows][:, cols].cpu().numpy()
         same_bits(got, oracle.gemv_dA(np.ascontiguousarray(dYr[:k]), np.ascontiguousarray(Xc[:k])))
     del dA, gi, A
+    torch.cuda.empty_cache()
+
+
+def test_dot_adjoint_full_size():
+    """The dot of 2^26 values at cond 1e12 (bench.py's workload) through the
+    autograd function: dx = Mul22(dout, y) and dy = Mul22(dout, x) bit for
+    bit against the oracle on 2^20 sampled indices plus both ends, and two
+    sampled entries of dx against central finite differences of the exact
+    dot (binary128 superaccumulator over all 2^26 terms)."""
+    import math
+    n = 1 << 26
+    g = inputs.ill_dot(n, 1e12, inputs.seed_for(2, 12), device=DEV)
+    dout = inputs.scalar_ff(321)
+    x = g.x.clone().requires_grad_(True)
+    y = g.y.clone().requires_grad_(True)
+    ff.ffdot(x, y).backward(dout.to(DEV))
+    gen = torch.Generator().manual_seed(99)
+    idx = torch.cat([torch.arange(1024), torch.randint(0, n, (1 << 20,), generator=gen),
+                     torch.arange(n - 1024, n)]).to(DEV)
+    xs, ys = g.x[idx].cpu().numpy(), g.y[idx].cpu().numpy()
+    dx_want, dy_want = oracle.dot_backward(dout.numpy(), xs, ys)
+    same_bits(x.grad[idx].cpu().numpy(), dx_want)
+    same_bits(y.grad[idx].cpu().numpy(), dy_want)
+    xn, yn = g.x.cpu().numpy(), g.y.cpu().numpy()
+    dval = float(dout[0]) + float(dout[1])
+    rng = np.random.default_rng(7)
+    for i in rng.choice(n, size=2, replace=False):
+        hi = float(xn[i, 0])
+        h = 2.0 ** (math.floor(math.log2(abs(hi))) - 10)
+        old = xn[i, 0]
+        xn[i, 0] = np.float32(hi + h)
+        sp = oracle.exact_dot(xn, yn)
+        xn[i, 0] = np.float32(hi - h)
+        sm = oracle.exact_dot(xn, yn)
+        xn[i, 0] = old
+        fd = dval * ((sp[0] - sm[0]) + (sp[1] - sm[1])) / (2.0 * h)
+        got = float(x.grad[i, 0]) + float(x.grad[i, 1])
+        assert abs(got - fd) <= (2.0 ** -44 + 2.0 ** -50) * abs(fd)
+    del g, x, y
     torch.cuda.empty_cache()
