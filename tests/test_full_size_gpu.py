@@ -168,3 +168,35 @@ def test_dot_adjoint_full_size():
         assert abs(got - fd) <= (2.0 ** -44 + 2.0 ** -50) * abs(fd)
     del g, x, y
     torch.cuda.empty_cache()
+
+
+def test_gemv_family_beyond_2_31_elements():
+    """A 65600 x 32768 matrix (2.15e9 elements, past 2^31, 17 GB): every
+    offset into A, dA and the adjoint's workspace needs 64 bits.  Rows and
+    columns sampled near both ends: Y and dX bit for bit against the
+    replays of their orders, dA (k = 1) against the oracle."""
+    import replay
+    from paper_cs_0603115_gb300 import _lib
+    M, N = 65600, 32768
+    assert M * N > 2 ** 31
+    gi = inputs.gemv(M, N, 1, inputs.seed_for(4, 190), device=DEV)
+    A = gi.A
+    rows = [0, 1, 32767, 32768, 65535, 65536, M - 2, M - 1]
+    cols = [0, 1, 16383, 16384, N - 2, N - 1]
+    Y = ff.gemv(A, gi.X)
+    dX = ff.gemv_t(A, gi.dY)
+    torch.cuda.synchronize()
+    same_bits(Y[:, rows].cpu().numpy(), replay.gemv_warp_replay(A[rows].cpu().numpy(), gi.X.cpu().numpy(), vec=True))
+    nrb, vec = ctypes.c_int64(), ctypes.c_int()
+    _lib.call("ff_gemv_t_launch_shape", A.data_ptr(), M, N, N, 1, ctypes.byref(nrb), ctypes.byref(vec))
+    same_bits(dX[:, cols].cpu().numpy(),
+              replay.gemv_t_replay(A[:, cols].cpu().numpy(), gi.dY.cpu().numpy(), nrb.value))
+    del Y, dX
+    dA = torch.empty_like(A)
+    ff.gemv_dA(gi.dY, gi.X, out=dA)
+    torch.cuda.synchronize()
+    got = dA[rows][:, cols].cpu().numpy()
+    same_bits(got, oracle.gemv_dA(np.ascontiguousarray(gi.dY[:, rows].cpu().numpy()),
+                                  np.ascontiguousarray(gi.X[:, cols].cpu().numpy())))
+    del dA, gi, A
+    torch.cuda.empty_cache()
