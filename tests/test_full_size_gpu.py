@@ -200,3 +200,21 @@ def test_gemv_family_beyond_2_31_elements():
                                   np.ascontiguousarray(gi.X[:, cols].cpu().numpy())))
     del dA, gi, A
     torch.cuda.empty_cache()
+
+
+def test_gemm_beyond_2_31_elements():
+    """C = A B of 65600 x 32768 (2.15e9 elements, past 2^31) with k = 3:
+    rows sampled near both ends bit for bit against the oracle's in-order
+    loop (64-bit offsets into C)."""
+    M, N, K = 65600, 32768, 3
+    gen = torch.Generator(device=DEV).manual_seed(inputs.seed_for(6, 190))
+    A = inputs.to_ff(inputs.loguniform_f64(M * K, gen, DEV)).reshape(M, K, 2)
+    B = inputs.to_ff(inputs.loguniform_f64(K * N, gen, DEV)).reshape(K, N, 2)
+    C = ff.gemm(A, B)
+    torch.cuda.synchronize()
+    rows = [0, 1, 32767, 32768, 65535, 65536, M - 1]
+    got = C[rows].cpu().numpy()
+    want = oracle.gemm(np.ascontiguousarray(A[rows].cpu().numpy()), B.cpu().numpy())
+    same_bits(got, want)
+    del C, A, B
+    torch.cuda.empty_cache()
