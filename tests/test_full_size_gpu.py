@@ -218,3 +218,31 @@ def test_gemm_beyond_2_31_elements():
     same_bits(got, want)
     del C, A, B
     torch.cuda.empty_cache()
+
+
+def test_batched_instance_beyond_2_31_values():
+    """One AXPY instance of 2^31 + 5 values (17 GB per array) next to a small
+    dot instance in one batched plan: the values near both ends and around
+    2^31 bit for bit against the oracle (64-bit tile offsets)."""
+    from paper_cs_0603115_gb300 import batch
+    n = (1 << 31) + 5
+    gen = torch.Generator(device=DEV).manual_seed(inputs.seed_for(3, 190))
+    x = inputs.to_ff(inputs.loguniform_f64(n, gen, DEV))
+    y = inputs.to_ff(inputs.loguniform_f64(n, gen, DEV))
+    z = torch.empty_like(x)
+    d = torch.empty(2, dtype=torch.float32, device=DEV)
+    alpha = (1.25, 2.0 ** -30)
+    plan = batch.BatchPlan(batch.make_instances([(batch.AXPY, x, y, z, alpha),
+                                                 (batch.DOT, x[:1000], y[:1000], d, None)]))
+    plan.run()
+    torch.cuda.synchronize()
+    # contiguous slices copied to the host (no gather kernel: PyTorch's
+    # index kernel asserted on an index tensor into these 2^31 + 5 rows)
+    spans = [(0, 4096), ((1 << 31) - 4096, (1 << 31) + 4096), (n - 4096, n)]
+    take = lambda t: np.concatenate([t[lo:hi].cpu().numpy() for lo, hi in spans])
+    same_bits(take(z), oracle.axpy(np.array(alpha, np.float32), take(x), take(y)))
+    _, _, a_abs, err = oracle.exact_dot(x[:1000].cpu().numpy(), y[:1000].cpu().numpy(), d.cpu().numpy())
+    assert abs(err) <= 1000 * 2.0 ** -46 * a_abs
+    plan.close()
+    del x, y, z
+    torch.cuda.empty_cache()
